@@ -1,0 +1,241 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+* closed form: 1D chain with node 0 fixed, K^{-1}_{ij} = h min(i, j);
+* brute force: numpy.linalg.inv(K_reg) gathered by B on tiny grids;
+* independent solve: conjugate gradients on sparse K_reg for F lambda;
+* invariants: symmetry, PSD, coefficient scaling, fixed-dof rows,
+  duplicate-dof columns;
+* planted mistakes: each plausible slip in the oracle makes a pin fail.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+import synth
+
+
+def _brute(sd):
+    A = np.asarray(sd.K.todense(), float)
+    f = np.asarray(sd.fixed)
+    A[f, :] = 0
+    A[:, f] = 0
+    A[f, f] = 1
+    Bt = sd.Bt.toarray()
+    return Bt.T @ np.linalg.inv(A) @ Bt
+
+
+def _random_bt_subdomain(sd, m, seed, multi=False):
+    """Same K, random B^T: signed unit columns, duplicates allowed, optionally
+    a few columns with several nonzeros (general gluing)."""
+    rng = np.random.default_rng(seed)
+    n = sd.n
+    rows, cols, vals = [], [], []
+    for j in range(m):
+        k = rng.integers(1, 4) if (multi and j % 5 == 0) else 1
+        for r in rng.choice(n, size=k, replace=False):
+            rows.append(r)
+            cols.append(j)
+            vals.append(rng.choice([-1.0, 1.0]))
+    Bt = sp.csc_matrix((vals, (rows, cols)), shape=(n, m))
+    return synth.Subdomain(K=sd.K, fixed=sd.fixed, Bt=Bt, lambda_map=np.arange(m),
+                           grid=sd.grid, ndpn=sd.ndpn, key=None)
+
+
+# ---------------------------------------------------------------- closed form
+
+@pytest.mark.parametrize("nel", [1, 7, 40])
+def test_chain_closed_form(nel):
+    rng = np.random.default_rng(nel)
+    sel = rng.integers(0, nel + 1, size=12)
+    sel[0] = 0                                    # the fixed node is selected too
+    signs = rng.choice([-1.0, 1.0], size=12)
+    sd = synth.chain_1d(nel, sel, signs)
+    F = oracle.dual_operator(sd)
+    h = 1.0 / nel
+    ref = np.empty((12, 12))
+    for a in range(12):
+        for b in range(12):
+            ia, ib = sel[a], sel[b]
+            if ia == 0 or ib == 0:                 # fixed dof: K_reg^{-1} e_0 = e_0
+                g = 1.0 if ia == ib else 0.0
+            else:
+                g = h * min(ia, ib)
+            ref[a, b] = signs[a] * signs[b] * g
+    assert np.max(np.abs(F - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- brute force
+
+def _tiny_cases():
+    out = []
+    for k in (2, 3, 4):
+        out.append(("q1_%d" % k, synth.single_heat_2d(k).subdomains[0]))
+    out.append(("config1", synth.single_heat_2d(16).subdomains[0]))
+    p = synth.cube_heat_3d(parts=2, k=2)
+    out += [("hex_%d" % i, s) for i, s in enumerate(p.subdomains[:3])]
+    p = synth.elasticity_cubes((2, 1, 1), 1, 2, seed=3)
+    out += [("elast_%d" % i, s) for i, s in enumerate(p.subdomains)]
+    return out
+
+
+@pytest.mark.parametrize("name,sd", _tiny_cases(), ids=lambda x: x if isinstance(x, str) else "")
+def test_brute_force_inverse(name, sd):
+    F = oracle.dual_operator(sd)
+    ref = _brute(sd)
+    assert oracle.relative_frobenius(F, ref) < 1e-13
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_brute_force_general_bt(multi):
+    base = synth.elasticity_cubes((1, 1, 1), 2, 2, seed=1).subdomains[0]
+    sd = _random_bt_subdomain(base, 30, seed=11, multi=multi)
+    assert oracle.relative_frobenius(oracle.dual_operator(sd), _brute(sd)) < 1e-12
+
+
+def test_cholesky_against_definition():
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((150, 150))
+    A = M @ M.T + 150 * np.eye(150)
+    G = oracle.cholesky(A, block=32)
+    assert np.allclose(np.triu(G, 1), 0)
+    assert np.abs(G @ G.T - A).max() < 1e-11 * np.abs(A).max()
+    with pytest.raises(oracle.NotSPDError):
+        oracle.cholesky(-A)
+
+
+# ---------------------------------------------------------------- independent solve
+
+def _cg_apply(sd, lam):
+    """B K_reg^{-1} B^T lambda by conjugate gradients on sparse K_reg (no factorisation)."""
+    K = sp.lil_matrix(sd.K, dtype=float)
+    for f in sd.fixed:
+        K[f, :] = 0
+        K[:, f] = 0
+        K[f, f] = 1
+    K = K.tocsr()
+    rhs = sd.Bt @ lam
+    x, info = spla.cg(K, rhs, rtol=1e-15, atol=0.0, maxiter=20000)
+    assert info == 0 or np.linalg.norm(K @ x - rhs) < 1e-12 * np.linalg.norm(rhs)
+    return sd.Bt.T @ x
+
+
+@pytest.mark.parametrize("which", ["config1", "heat3d", "elast"])
+def test_apply_matches_cg(which):
+    if which == "config1":
+        sd = synth.make_config(1).subdomains[0]
+    elif which == "heat3d":
+        sd = synth.cube_heat_3d(parts=2, k=5).subdomains[3]
+    else:
+        sd = synth.elasticity_cubes((2, 1, 1), 3, 3, seed=2).subdomains[0]
+    F = oracle.dual_operator(sd)
+    lam = np.random.default_rng(5).standard_normal(sd.m)
+    ref = _cg_apply(sd, lam)
+    assert np.linalg.norm(F @ lam - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_symmetry_and_psd_config1():
+    F = oracle.dual_operator(synth.make_config(1).subdomains[0])
+    assert np.abs(F - F.T).max() <= 1e-14 * np.abs(F).max()
+    ev = np.linalg.eigvalsh(0.5 * (F + F.T))
+    assert ev.min() >= -1e-12 * ev.max()
+
+
+def test_duplicate_dofs_and_fixed_rows():
+    p = synth.cube_heat_3d(parts=2, k=3)
+    for sd in p.subdomains:
+        F = oracle.dual_operator(sd)
+        dof = sd.Bt.indices
+        sgn = sd.Bt.data
+        for a in range(sd.m):
+            same = np.nonzero(dof == dof[a])[0]
+            for b in same:                      # columns on the same dof: equal up to sign
+                assert np.allclose(F[:, a] * sgn[a], F[:, b] * sgn[b], rtol=0, atol=1e-13)
+            if dof[a] in sd.fixed:              # fixed dof: row is +-1 on its own dof, else 0
+                expect = np.where(dof == dof[a], sgn * sgn[a], 0.0)
+                assert np.allclose(F[a], expect, atol=1e-14)
+
+
+def test_coefficient_scaling():
+    """K -> c K leaves the fixed-dof block alone and scales the rest of F by 1/c."""
+    unit = synth.cube_heat_3d(parts=2, k=3)
+    scaled = synth.cube_heat_3d(parts=2, k=3, coef_seed=9)
+    memo = oracle._Memo()
+    for su, ss in zip(unit.subdomains, scaled.subdomains):
+        c = ss.K[0, 0] / su.K[0, 0]
+        assert not np.isclose(c, 1.0)
+        Fu = oracle.dual_operator(su, memo)
+        Fs = oracle.dual_operator(ss, memo)
+        fixed = np.isin(su.Bt.indices, su.fixed)
+        free = ~fixed
+        assert np.allclose(Fs[np.ix_(free, free)], Fu[np.ix_(free, free)] / c, rtol=1e-12, atol=0)
+        assert np.allclose(Fs[np.ix_(fixed, fixed)], Fu[np.ix_(fixed, fixed)], atol=1e-15)
+
+
+def test_apply_dual_sums_subdomains():
+    p = synth.cube_heat_3d(parts=2, k=2)
+    Fs = oracle.dual_operators(p.subdomains)
+    lam = np.random.default_rng(1).standard_normal(p.n_dual)
+    q = oracle.apply_dual(Fs, [s.lambda_map for s in p.subdomains], lam, p.n_dual)
+    ref = np.zeros(p.n_dual)
+    for s, F in zip(p.subdomains, Fs):
+        Bfull = np.zeros((s.m, p.n_dual))
+        Bfull[np.arange(s.m), s.lambda_map] = 1.0
+        ref += Bfull.T @ F @ Bfull @ lam
+    assert np.allclose(q, ref, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _pins_pass():
+    try:
+        test_chain_closed_form(7)
+        for name, sd in _tiny_cases()[:4]:
+            test_brute_force_inverse(name, sd)
+        return True
+    except (AssertionError, oracle.NotSPDError, ValueError, FloatingPointError):
+        return False
+
+
+def _bad_regularize(K, f):
+    A = _ORIG["regularize"](K, f)
+    A[np.asarray(f), np.asarray(f)] = 2.0          # wrong diagonal on fixed dofs
+    return A
+
+
+def _bad_backward(G, Z, block=64):
+    return oracle.forward_substitution(G, Z, block)  # G^{-1} where G^{-T} belongs
+
+
+def _bad_cholesky(A, block=64):
+    A = np.array(A, float)                          # trailing update dropped
+    n = A.shape[0]
+    for k0 in range(0, n, block):
+        k1 = min(k0 + block, n)
+        Gkk = oracle._cholesky_unblocked(A[k0:k1, k0:k1])
+        A[k0:k1, k0:k1] = Gkk
+        if k1 < n:
+            A[k1:, k0:k1] = oracle._lower_solve_small(Gkk, A[k1:, k0:k1].T).T
+    return np.tril(A)
+
+
+def _unsigned_dual_operator(sd, memo=None):
+    sd2 = synth.Subdomain(K=sd.K, fixed=sd.fixed, Bt=abs(sd.Bt), lambda_map=sd.lambda_map,
+                          grid=sd.grid, ndpn=sd.ndpn, key=None)
+    return _ORIG["dual_operator"](sd2, memo)     # signs of B dropped
+
+
+_ORIG = {"regularize": oracle.regularize, "dual_operator": oracle.dual_operator}
+
+
+@pytest.mark.parametrize("name,bad", [("regularize", _bad_regularize),
+                                      ("backward_substitution", _bad_backward),
+                                      ("cholesky", _bad_cholesky),
+                                      ("dual_operator", _unsigned_dual_operator)])
+def test_pins_catch_planted_mistakes(monkeypatch, name, bad):
+    assert _pins_pass()
+    monkeypatch.setattr(oracle, name, bad)
+    assert not _pins_pass()
