@@ -1,0 +1,208 @@
+/* sc.h -- GPU assembly and application of FETI local dual operators
+ *         (dense Schur complements) on GB300 (sm_103a), C ABI.
+ *
+ * What is computed (paper Sec. 2.1-2.2, Eq. "localdualoperator",
+ * Eq. "localdualoperatorwithU"; Sec. 3.1, the Y^T Y form):
+ *
+ *     F_i = B_i K_i^+ B_i^T = B_i L_i^{-T} L_i^{-1} B_i^T = Y_i^T Y_i,
+ *     Y_i = L_i^{-1} B_i^T,
+ *
+ * for every subdomain i of a batch, from the sparse Cholesky factor L_i of the
+ * regularised subdomain matrix (already permuted by the fill-reducing
+ * ordering P, so B_i^T's rows are given in L_i's ordering; paper Sec. 3), and
+ * the explicit application q = sum_i B_i^T-scatter(F_i lambda_i)
+ * (Eq. "dualop_apply_expl").
+ *
+ * Method (paper Sec. 3.2-3.3): the columns of B_i^T are sorted by their column
+ * pivot (first nonzero in L's ordering; with an etree-postordered L this is
+ * the paper's "stepped" shape), the forward substitution skips the zero rows
+ * above the pivots and the structurally zero blocks of L ("factor splitting"
+ * with "pruning" of empty rows), and the SYRK Y^T Y forms only the blocks of
+ * the lower triangle whose inputs are structurally nonzero ("input splitting").
+ * Here the blocks are the supernodes of L and the column range of Y that is
+ * nonzero on each supernode.  Finally F is permuted back to B_i^T's original
+ * column order (paper Sec. 3, end of the preamble).
+ *
+ * Stages (paper Sec. 2.2, the three solver stages):
+ *   initialization -- sc_plan (host, symbolic only: patterns, never values),
+ *                     sc_get_sizes, sc_upload_plan (plan tables to the GPU);
+ *   preprocessing  -- sc_assemble_batch (numeric: new L values, same patterns);
+ *   solution       -- sc_apply once per iteration of the dual solver.
+ *
+ * Memory: the caller owns every device buffer (plan tables, workspace, L
+ * values, F, lambda, q).  F is persistent; the workspace is temporary and may
+ * be reused by anything else between calls (paper Sec. 3.1, persistent vs
+ * temporary memory).  The library itself allocates host memory only.
+ *
+ * Streams: every device call takes a cudaStream_t passed as void*; NULL is the
+ * legacy default stream.  Calls are asynchronous unless stated otherwise.
+ *
+ * Errors: every call returns an sc_status; nothing is thrown across the ABI.
+ * The message of the last failing call on a context is sc_last_error(ctx).
+ * Device-side failures (non-positive or non-finite diagonal of L) are recorded
+ * in the workspace's status word and reported by sc_device_status; F is then
+ * undefined.
+ *
+ * Precision: FP64 throughout (IEEE binary64 multiply-add, round to nearest).
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sc_ctx sc_ctx; /* opaque plan + state, owned by the library */
+
+typedef enum {
+  SC_OK = 0,
+  SC_ERR_INVALID_ARG = 1, /* bad size, pointer, pattern or option */
+  SC_ERR_NOT_SPD = 2,     /* a diagonal entry of L is not positive and finite */
+  SC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has details) */
+  SC_ERR_OOM = 4,         /* a buffer passed is smaller than sc_get_sizes asks */
+  SC_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (reserved) */
+  SC_ERR_INTERNAL = 6,
+  SC_ERR_STATE = 7        /* call out of order (e.g. assemble before upload) */
+} sc_status;
+
+/* One subdomain, host arrays.  They are read during sc_plan only (patterns are
+ * copied into the plan); values never pass through sc_plan.
+ *   n, m        -- dofs of the subdomain, multipliers touching it (columns of B^T)
+ *   L_colptr    -- [n+1] int64, CSC column pointers of L (lower, P K_reg P^T)
+ *   L_rowind    -- [L_colptr[n]] int32, rows ascending, diagonal first per column
+ *   Bt_colptr   -- [m+1] int32, CSC of B_i^T (n x m)
+ *   Bt_rowind   -- [Bt_colptr[m]] int32, rows in L's ordering, ascending per column
+ *   Bt_sign     -- [Bt_colptr[m]] int8, the entries of B_i^T (+1 or -1)
+ *   lambda_map  -- [m] int32, local column -> global multiplier index
+ *                  (used by sc_apply; may be NULL if sc_apply is never called)
+ * Any number of nonzeros per column of B^T is accepted (general gluing); the
+ * FETI case has exactly one. */
+typedef struct {
+  int32_t n, m;
+  const int64_t *L_colptr;
+  const int32_t *L_rowind;
+  const int32_t *Bt_colptr;
+  const int32_t *Bt_rowind;
+  const int8_t *Bt_sign;
+  const int32_t *lambda_map;
+} sc_subdomain_desc;
+
+enum { SC_FP64 = 0 };
+
+typedef struct {
+  int32_t precision;   /* SC_FP64 */
+  int32_t reserved[7]; /* must be zero */
+} sc_options;
+
+typedef struct {
+  size_t plan_bytes;       /* device plan tables (sc_upload_plan) */
+  size_t ws_bytes;         /* device workspace for sc_assemble_batch */
+  int64_t F_doubles;       /* total doubles of all F_i (layout below) */
+  int64_t L_values;        /* total entries of all L_i = sum_i L_colptr_i[n_i] */
+  int32_t nsub;
+  int32_t max_m;
+} sc_sizes;
+
+/* Per-batch counters of the plan (host, exact integers). */
+typedef struct {
+  double flops_trsm;        /* useful flops of the sparse forward substitution */
+  double flops_syrk;        /* useful flops of the pruned SYRK (lower triangle) */
+  double flops_trsm_exec;   /* flops the kernels issue (incl. 32-lane padding) */
+  double flops_syrk_exec;
+  double flops_dense;       /* sum_i n_i^2 m_i + n_i m_i (m_i + 1): the dense TRSM+SYRK yardstick */
+  double bytes_assembly;    /* algorithmic bytes: 12 nnz(L) + 8 m(m+1)/2 per subdomain */
+  double bytes_apply;       /* algorithmic bytes of sc_apply: 8 m(m+1)/2 + 16 m per subdomain */
+  int64_t n_supernodes;     /* active supernodes (touched by some column) */
+  int64_t n_trsm_tasks, n_syrk_tasks, n_apply_tasks;
+  int64_t y_doubles;        /* workspace doubles of the sparse Y */
+} sc_stats;
+
+/* ---- initialization -------------------------------------------------------- */
+
+/* Validate the patterns and build the plan (host only; no CUDA call).
+ * n_dual: length of the global dual vectors lambda and q (>= 1 + max lambda_map).
+ * opt may be NULL (FP64 defaults).  *out is set whenever a context could be
+ * allocated -- also on failure, so that sc_last_error(*out) explains it -- and
+ * must be released with sc_destroy. */
+sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomains,
+                  int64_t n_dual, const sc_options *opt);
+
+sc_status sc_get_sizes(const sc_ctx *ctx, sc_sizes *out);
+sc_status sc_get_stats(const sc_ctx *ctx, sc_stats *out);
+
+/* F layout.  F_i (m_i x m_i, symmetric, rows/columns in B_i^T's column order)
+ * is stored as its lower 32x32 tiles: tile (I, J), I >= J, is the block
+ * rows [32I, 32I+32) x columns [32J, 32J+32); tiles are ordered I(I+1)/2 + J;
+ * each tile is 1024 doubles, column-major; diagonal tiles hold both triangles;
+ * entries beyond m_i are zero.  F_i starts at F_offsets[i] (doubles);
+ * F_offsets has nsub+1 entries.  L values of subdomain i start at
+ * L_offsets[i] in the concatenated L value array (nsub+1 entries). */
+sc_status sc_get_offsets(const sc_ctx *ctx, int64_t *F_offsets, int64_t *L_offsets);
+
+/* Copy the plan tables into caller-owned device memory of at least plan_bytes
+ * (16-byte aligned); the context remembers the pointer for later calls.  The
+ * copy is ordered on `stream`; the host tables stay owned by the context. */
+sc_status sc_upload_plan(sc_ctx *ctx, void *plan_dev, size_t plan_bytes, void *stream);
+
+/* ---- preprocessing ----------------------------------------------------------- */
+
+/* Assemble every F_i from new L values (same patterns as planned).
+ *   L_values_dev -- device, concatenated CSC values of all L_i (sizes.L_values)
+ *   F_dev        -- device, sizes.F_doubles, written completely (padding zeroed)
+ *   ws_dev       -- device workspace, >= sizes.ws_bytes, 256-byte aligned;
+ *                   its contents on entry do not matter
+ * Asynchronous on `stream`; check sc_device_status after completion. */
+sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_dev,
+                            void *ws_dev, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and reads the device status word in ws_dev:
+ * SC_OK, or SC_ERR_NOT_SPD when a diagonal of L was not positive and finite. */
+sc_status sc_device_status(sc_ctx *ctx, const void *ws_dev, void *stream);
+
+/* ---- solution ------------------------------------------------------------------ */
+
+/* q = sum_i scatter_i(F_i * gather_i(lambda))  (Eq. "dualop_apply_expl" summed
+ * over subdomains).  lambda_dev, q_dev: device, n_dual doubles each; q is
+ * overwritten (the library zeroes it first).  Asynchronous on `stream`. */
+sc_status sc_apply(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
+                   void *stream);
+
+/* Expand F_i into a dense full m_i x m_i column-major device matrix dst_dev
+ * with leading dimension ld >= m_i.  Asynchronous on `stream`. */
+sc_status sc_export_F(sc_ctx *ctx, const double *F_dev, int32_t i, double *dst_dev, int32_t ld,
+                      void *stream);
+
+/* ---- misc ---------------------------------------------------------------------- */
+
+/* Stage timing.  With timing on, sc_assemble_batch records a CUDA event on its
+ * stream before the first kernel and after each stage: [0] prep (reciprocal
+ * diagonal, F padding), [1] sparse TRSM, [2] pruned SYRK.  sc_stage_times
+ * synchronises on the last recorded event and writes up to n elapsed times
+ * (milliseconds) of the last timed call.  Events are created by
+ * sc_enable_stage_timing(ctx, 1) on the current device and destroyed by
+ * sc_enable_stage_timing(ctx, 0) or sc_destroy. */
+sc_status sc_enable_stage_timing(sc_ctx *ctx, int32_t on);
+sc_status sc_stage_times(sc_ctx *ctx, float *ms, int32_t n);
+
+/* Copy the plan tables (exactly sizes.plan_bytes) into host memory `dst`.  The
+ * blob starts with a 512-byte self-describing header (magic "SCPL", version,
+ * counts, section offsets and sizes); it is what sc_upload_plan copies to the
+ * device, so it can be stored and inspected.  SC_ERR_OOM if bytes is too small. */
+sc_status sc_export_plan(const sc_ctx *ctx, void *dst, size_t bytes);
+
+/* Byte offsets inside the workspace: the 4-byte device status word, the
+ * reciprocal diagonal of L (one double per column of every subdomain) and
+ * the sparse Y blocks (sizes/stats.y_doubles doubles). */
+sc_status sc_workspace_layout(const sc_ctx *ctx, size_t *status_off, size_t *invdiag_off, size_t *y_off);
+
+const char *sc_last_error(const sc_ctx *ctx);
+void sc_destroy(sc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_H */

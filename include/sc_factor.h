@@ -1,0 +1,53 @@
+/* Host sparse Cholesky producing the factor L consumed by the Schur-complement
+ * library (input producer, FP64, CPU only; not part of the GPU hot path).
+ *
+ * Paper Sec. 2.2 (two-stage factorisation, symbolic then numeric, of the
+ * regularised subdomain matrix K_reg = L L^T; K^+ = K_reg^{-1}).
+ *
+ * Conventions
+ *   - K is passed in full symmetric CSC (both triangles), original dof order,
+ *     int64 column pointers, int32 row indices, FP64 values.  Host memory,
+ *     owned by the caller, only read during the call.
+ *   - fixed[] lists the dofs fixed to regularise a floating subdomain: their
+ *     rows and columns are replaced by the identity (fixing-node reading of
+ *     the paper's regularisation).
+ *   - perm_in[new] = old is the fill-reducing ordering (NULL = identity).  With
+ *     do_postorder != 0 the etree postorder is composed into it; the final
+ *     ordering is returned by scf_export.
+ *   - The factor is CSC lower triangular of P K_reg P^T, rows ascending,
+ *     diagonal first in each column.  The handle owns it until scf_free.
+ * Errors: SCF_ERR_INVALID_ARG (bad sizes, indices or permutation),
+ *         SCF_ERR_NOT_SPD (non-positive or non-finite pivot), SCF_ERR_OOM.
+ *         No partial result is returned on error (*out stays NULL).
+ */
+#ifndef SC_FACTOR_H
+#define SC_FACTOR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { SCF_OK = 0, SCF_ERR_INVALID_ARG = 1, SCF_ERR_NOT_SPD = 2, SCF_ERR_OOM = 3 };
+
+typedef struct scf_factor scf_factor;
+
+int scf_factorize(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, const double *K_val,
+                  int32_t nfixed, const int32_t *fixed, const int32_t *perm_in, int32_t do_postorder,
+                  scf_factor **out);
+
+/* number of stored entries of L (lower triangle incl. diagonal); -1 on NULL */
+int64_t scf_nnz(const scf_factor *f);
+
+/* copy L out: colptr[n+1], rowind[nnz], val[nnz], perm[n] (new -> old); any
+ * pointer may be NULL to skip that array */
+int scf_export(const scf_factor *f, int64_t *colptr, int32_t *rowind, double *val, int32_t *perm);
+
+void scf_free(scf_factor *f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_FACTOR_H */

@@ -1,0 +1,78 @@
+"""ctypes mirror of include/sc.h and include/sc_dense.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+c_i8p = ctypes.c_void_p
+c_vp = ctypes.c_void_p
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_sz = ctypes.c_size_t
+c_int = ctypes.c_int
+
+STATUS = {0: "SC_OK", 1: "SC_ERR_INVALID_ARG", 2: "SC_ERR_NOT_SPD", 3: "SC_ERR_CUDA", 4: "SC_ERR_OOM",
+          5: "SC_ERR_TIMEOUT", 6: "SC_ERR_INTERNAL", 7: "SC_ERR_STATE"}
+SC_OK, SC_ERR_INVALID_ARG, SC_ERR_NOT_SPD, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_TIMEOUT, SC_ERR_INTERNAL, SC_ERR_STATE = range(8)
+
+
+class SubdomainDesc(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("m", c_i32), ("L_colptr", c_vp), ("L_rowind", c_vp),
+                ("Bt_colptr", c_vp), ("Bt_rowind", c_vp), ("Bt_sign", c_vp), ("lambda_map", c_vp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_i32), ("reserved", c_i32 * 7)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("plan_bytes", c_sz), ("ws_bytes", c_sz), ("F_doubles", c_i64), ("L_values", c_i64),
+                ("nsub", c_i32), ("max_m", c_i32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("flops_trsm", ctypes.c_double), ("flops_syrk", ctypes.c_double),
+                ("flops_trsm_exec", ctypes.c_double), ("flops_syrk_exec", ctypes.c_double),
+                ("flops_dense", ctypes.c_double), ("bytes_assembly", ctypes.c_double),
+                ("bytes_apply", ctypes.c_double), ("n_supernodes", c_i64), ("n_trsm_tasks", c_i64),
+                ("n_syrk_tasks", c_i64), ("n_apply_tasks", c_i64), ("y_doubles", c_i64)]
+
+
+# every symbol include/sc.h declares, with (argtypes, restype)
+SC_SYMBOLS = {
+    "sc_plan": ([ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(SubdomainDesc), c_i64, ctypes.POINTER(Options)], c_int),
+    "sc_get_sizes": ([c_vp, ctypes.POINTER(Sizes)], c_int),
+    "sc_get_stats": ([c_vp, ctypes.POINTER(Stats)], c_int),
+    "sc_get_offsets": ([c_vp, c_vp, c_vp], c_int),
+    "sc_upload_plan": ([c_vp, c_vp, c_sz, c_vp], c_int),
+    "sc_assemble_batch": ([c_vp, c_vp, c_vp, c_vp, c_sz, c_vp], c_int),
+    "sc_device_status": ([c_vp, c_vp, c_vp], c_int),
+    "sc_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_export_F": ([c_vp, c_vp, c_i32, c_vp, c_i32, c_vp], c_int),
+    "sc_enable_stage_timing": ([c_vp, c_i32], c_int),
+    "sc_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), c_i32], c_int),
+    "sc_export_plan": ([c_vp, c_vp, c_sz], c_int),
+    "sc_workspace_layout": ([c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_last_error": ([c_vp], ctypes.c_char_p),
+    "sc_destroy": ([c_vp], None),
+}
+
+DENSE_SYMBOLS = {
+    "scd_create": ([ctypes.POINTER(c_vp), c_i32], c_int),
+    "scd_trsm_syrk": ([c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
+    "scd_destroy": ([c_vp], None),
+}
+
+
+def _declare(lib, table):
+    for name, (args, res) in table.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def declare(lib):
+    _declare(lib, SC_SYMBOLS)
+
+
+def declare_dense(lib):
+    _declare(lib, DENSE_SYMBOLS)

@@ -1,0 +1,152 @@
+// Internal plan layout shared by the host planner (sc_plan.cpp), the C ABI
+// (sc_api.cu) and the kernels (sc_kernels.cu).
+//
+// Vocabulary (paper Sec. 3): n dofs, m multipliers (columns of B^T), the column
+// pivot of a column is its first nonzero row in L's ordering; columns are
+// processed in "sorted" order (by pivot, via the etree postorder rank).  The
+// blocks of the factor splitting are the supernodes of L: a supernode s is a
+// chain of consecutive columns c0..c0+ns-1 whose patterns below the diagonal
+// block coincide; its "pruned rows" R_s (rs of them) are the nonempty rows
+// below the diagonal block.  Y restricted to the rows of s is nonzero only on
+// the sorted column range [jlo, jhi) and is stored densely there, row-major
+// (ns x ws, ws = jhi - jlo).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sc.h"
+
+namespace sc {
+
+constexpr int kChunk = 32;      // column chunk width of the TRSM / SYRK tasks
+constexpr int kTile = 32;       // F tile edge
+constexpr int kThreads = 128;   // threads per CTA of the assembly kernels
+
+struct SubDev {
+  int64_t F_off;     // doubles, start of F_i (tile-packed lower)
+  int64_t L_off;     // start of L_i's values in the concatenated value array
+  int32_t n, m, nt;  // nt = ceil(m / 32)
+  int32_t col_off;   // offset of this subdomain's m entries in perm_cols / lambda
+  int32_t lcp_off;   // offset of this subdomain's n entries in lcp / invdiag
+  int32_t pad;
+};
+
+struct SnDev {
+  int64_t y_off;     // doubles, start of Y_s in the Y region
+  int64_t rmap_off;  // first entry of this supernode in rmap
+  int32_t sub;       // subdomain
+  int32_t c0, ns, rs;
+  int32_t jlo, jhi;  // sorted column range on which Y_s is nonzero
+  int32_t lcp_off;   // global column index of c0 (index into lcp / invdiag)
+  int32_t cut_off;   // first entry of this supernode in cuts (one per 32-row block)
+};
+
+struct TrsmTask {
+  int32_t sub, c_lo, w;       // sorted columns [c_lo, c_lo + w)
+  int32_t list_off, list_len; // supernodes touched, ascending (children first)
+  int32_t seed_lo, seed_hi;   // seeds of these columns
+  int32_t pad;
+};
+
+struct SyrkTask {
+  int32_t sub, q1, q2;        // output block of sorted chunks q1 >= q2
+  int32_t list_off, list_len; // supernodes active on both chunks
+  int32_t pad[3];
+};
+
+struct Seed {
+  int64_t y_off;  // doubles in the Y region
+  double value;   // entry of B^T (+1 / -1)
+};
+
+struct ApplyTask {
+  int32_t sub, I;
+};
+
+// Device pointers into the uploaded plan blob.
+struct PlanPtrs {
+  const SubDev *subs;
+  const SnDev *sns;
+  const int64_t *lcp;        // absolute index of L(c, c) for every column of every subdomain
+  const int64_t *rmap;       // per pruned row: Y offset of (row, column jlo of its source supernode)
+  const TrsmTask *trsm_tasks;
+  const int32_t *trsm_list;
+  const SyrkTask *syrk_tasks;
+  const int32_t *syrk_list;
+  const Seed *seeds;
+  const int32_t *perm_cols;  // sorted position -> user column, per subdomain
+  const int32_t *lambda;     // user column -> global multiplier, per subdomain
+  const ApplyTask *apply_tasks;
+  const int32_t *active_cols; // global column indices whose reciprocal diagonal is needed
+  const int32_t *cuts;       // per supernode and 32-row block: sorted columns >= cut are zero there
+};
+
+struct Section {
+  size_t off = 0, bytes = 0;
+};
+
+// First kHeaderBytes (512) bytes of the plan blob: a self-describing header, so that the
+// host copy (sc_export_plan) can be inspected or stored.  Sections follow in
+// the order of the arrays below, each 256-byte aligned.
+constexpr int kNumSections = 14;
+struct PlanHeader {
+  uint32_t magic;      // 'SCPL'
+  uint32_t version;    // 1
+  int32_t nsub;
+  int32_t chunk;       // kChunk
+  int64_t n_sns, n_trsm, n_syrk, n_apply, n_cols, n_active_cols;
+  uint64_t sec_off[kNumSections];   // subs sns lcp rmap trsm trsm_list syrk syrk_list seeds perm lambda apply active cuts
+  uint64_t sec_bytes[kNumSections];
+};
+constexpr size_t kHeaderBytes = 512;
+static_assert(sizeof(PlanHeader) <= kHeaderBytes, "plan header must fit its reserved bytes");
+
+// Workspace layout (bytes from ws_dev): [status 256 B][invdiag][Y]
+struct WsLayout {
+  size_t status_off = 0;
+  size_t invd_off = 256;
+  size_t y_off = 0;
+  size_t total = 0;
+};
+
+}  // namespace sc
+
+struct sc_ctx {
+  std::string err;
+  int32_t nsub = 0;
+  int64_t n_dual = 0;
+  std::vector<uint8_t> blob;     // plan tables, 256-byte aligned sections
+  sc::Section s_subs, s_sns, s_lcp, s_rmap, s_trsm, s_trsm_list, s_syrk, s_syrk_list, s_seeds,
+      s_perm, s_lambda, s_apply, s_active, s_cuts;
+  int64_t n_sns = 0, n_trsm = 0, n_syrk = 0, n_apply = 0, n_cols = 0, n_active_cols = 0;
+  std::vector<int64_t> F_offsets, L_offsets;
+  std::vector<int32_t> n, m;
+  sc::WsLayout ws;
+  sc_sizes sizes{};
+  sc_stats stats{};
+  bool has_lambda = true;
+  void *plan_dev = nullptr;
+  size_t plan_dev_bytes = 0;
+  void *stage_events[4] = {nullptr, nullptr, nullptr, nullptr};  // cudaEvent_t, stage timing
+  bool stage_recorded = false;
+  ~sc_ctx();
+
+  sc::PlanPtrs ptrs() const;
+};
+
+namespace sc {
+
+sc_status fail(sc_ctx *ctx, sc_status st, const std::string &msg);
+
+// kernel launchers (sc_kernels.cu); return cudaError_t as int
+int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F,
+                void *stream);
+int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, double *Y, void *stream);
+int launch_syrk(const sc_ctx &c, const double *Y, double *F, void *stream);
+int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
+int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);
+
+}  // namespace sc

@@ -1,0 +1,177 @@
+"""Host-side input production: fill-reducing ordering and sparse Cholesky.
+
+The Schur-complement assembly starts from a *given* sparse Cholesky factor L
+of the regularised subdomain matrix (paper Sec. 2.2 and Sec. 3: the input is
+B^T together with L, both in the fill-reducing order of the symbolic
+factorisation).  This module produces that input on the CPU:
+
+  * ``nested_dissection`` -- geometric nested dissection on the structured
+    node grid (bisect the longest axis, separator plane ordered last, recurse
+    down to small leaf boxes; the dofs of a node stay contiguous).  The paper
+    uses METIS for this step; on structured grids geometric dissection gives
+    the same kind of ordering without a graph partitioner;
+  * ``factorize`` -- the native host Cholesky (libscfactor.so) on
+    P K_reg P^T, with the etree postorder composed into P;
+  * ``factorize_problem`` -- the above for every subdomain of a batch, with
+    identical (K, fixed) pairs factorised once (the factor is an input; the
+    GPU library still reads every subdomain's values separately).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from concurrent.futures import ThreadPoolExecutor
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import _native
+
+
+def nested_dissection(grid: Tuple[int, int, int], ndpn: int = 1, leaf: int = 8) -> np.ndarray:
+    """Dof permutation new -> old for a lexicographic (x fastest) node grid."""
+    nx, ny, nz = grid
+    order: List[np.ndarray] = []
+
+    def box_nodes(lo, hi):
+        xs, ys, zs = (np.arange(lo[a], hi[a]) for a in range(3))
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        return (X + nx * (Y + ny * Z)).ravel()
+
+    stack = [((0, 0, 0), (nx, ny, nz), False)]
+    # iterative post-order: left box, right box, then separator
+    out: List[np.ndarray] = []
+
+    def rec(lo, hi):
+        ext = [hi[a] - lo[a] for a in range(3)]
+        cnt = ext[0] * ext[1] * ext[2]
+        if cnt == 0:
+            return
+        if cnt <= leaf or max(ext) < 3:
+            out.append(box_nodes(lo, hi))
+            return
+        ax = int(np.argmax(ext))
+        mid = lo[ax] + ext[ax] // 2
+        lhi = list(hi); lhi[ax] = mid
+        rlo = list(lo); rlo[ax] = mid + 1
+        slo = list(lo); slo[ax] = mid
+        shi = list(hi); shi[ax] = mid + 1
+        rec(tuple(lo), tuple(lhi))
+        rec(tuple(rlo), tuple(hi))
+        out.append(box_nodes(tuple(slo), tuple(shi)))
+
+    rec((0, 0, 0), (nx, ny, nz))
+    nodes = np.concatenate(out)
+    assert len(nodes) == nx * ny * nz
+    return (nodes[:, None] * ndpn + np.arange(ndpn)[None, :]).ravel().astype(np.int32)
+
+
+@dataclasses.dataclass
+class HostFactor:
+    """L (CSC lower, rows ascending, diagonal first) of P K_reg P^T and P."""
+    n: int
+    colptr: np.ndarray   # int64 [n+1]
+    rowind: np.ndarray   # int32 [nnz]
+    values: np.ndarray   # float64 [nnz]
+    perm: np.ndarray     # int32 [n], new -> old
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colptr[-1])
+
+    @property
+    def iperm(self) -> np.ndarray:
+        ip = np.empty(self.n, np.int32)
+        ip[self.perm] = np.arange(self.n, dtype=np.int32)
+        return ip
+
+
+def factorize(K: sp.spmatrix, fixed: Sequence[int], perm: Optional[np.ndarray] = None,
+              postorder: bool = True) -> HostFactor:
+    lib = _native.factor_lib()
+    Kc = sp.csc_matrix(K)
+    Kc.sort_indices()
+    n = Kc.shape[0]
+    cp = np.ascontiguousarray(Kc.indptr, dtype=np.int64)
+    ri = np.ascontiguousarray(Kc.indices, dtype=np.int32)
+    va = np.ascontiguousarray(Kc.data, dtype=np.float64)
+    fx = np.ascontiguousarray(np.asarray(fixed), dtype=np.int32)
+    pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    h = ctypes.c_void_p()
+    rc = lib.scf_factorize(n, cp.ctypes.data, ri.ctypes.data, va.ctypes.data, len(fx),
+                           fx.ctypes.data if len(fx) else None,
+                           pm.ctypes.data if pm is not None else None, int(postorder), ctypes.byref(h))
+    if rc != 0:
+        raise RuntimeError(f"scf_factorize failed with code {rc}")
+    try:
+        nnz = lib.scf_nnz(h)
+        out = HostFactor(n, np.empty(n + 1, np.int64), np.empty(nnz, np.int32),
+                         np.empty(nnz, np.float64), np.empty(n, np.int32))
+        lib.scf_export(h, out.colptr.ctypes.data, out.rowind.ctypes.data, out.values.ctypes.data,
+                       out.perm.ctypes.data)
+    finally:
+        lib.scf_free(h)
+    return out
+
+
+@dataclasses.dataclass
+class FactoredSubdomain:
+    """Library input for one subdomain: L in the fill-reducing order and B^T
+    with rows renumbered into that order (columns untouched)."""
+    L: HostFactor
+    bt_colptr: np.ndarray   # int32 [m+1]
+    bt_rowind: np.ndarray   # int32 [nnz(B^T)], rows in L's ordering
+    bt_sign: np.ndarray     # int8  [nnz(B^T)]
+    lambda_map: np.ndarray  # int32 [m]
+
+    @property
+    def n(self) -> int:
+        return self.L.n
+
+    @property
+    def m(self) -> int:
+        return len(self.bt_colptr) - 1
+
+
+def permute_bt(sd, L: HostFactor) -> FactoredSubdomain:
+    Bt = sp.csc_matrix(sd.Bt)
+    ip = L.iperm
+    rows = ip[Bt.indices]
+    cp = Bt.indptr.astype(np.int32)
+    # rows ascending within each column
+    ri = rows.astype(np.int32).copy()
+    sg = np.sign(Bt.data).astype(np.int8)
+    for j in range(Bt.shape[1]):
+        a, b = cp[j], cp[j + 1]
+        if b - a > 1:
+            o = np.argsort(ri[a:b], kind="stable")
+            ri[a:b] = ri[a:b][o]
+            sg[a:b] = sg[a:b][o]
+    return FactoredSubdomain(L, cp, ri, sg, np.asarray(sd.lambda_map, np.int32))
+
+
+def factorize_problem(subdomains, threads: int = 0, leaf: int = 8) -> List[FactoredSubdomain]:
+    """Order and factorise every subdomain (identical keys factorised once)."""
+    keys: Dict[object, int] = {}
+    uniq = []
+    for sd in subdomains:
+        k = sd.key if sd.key is not None else id(sd)
+        if k not in keys:
+            keys[k] = len(uniq)
+            uniq.append(sd)
+
+    def work(sd):
+        p = nested_dissection(sd.grid, sd.ndpn, leaf)
+        return factorize(sd.K, sd.fixed, p, postorder=True)
+
+    if threads == 1 or len(uniq) == 1:
+        facs = [work(sd) for sd in uniq]
+    else:
+        with ThreadPoolExecutor(max_workers=threads or None) as ex:
+            facs = list(ex.map(work, uniq))
+    out = []
+    for sd in subdomains:
+        k = sd.key if sd.key is not None else id(sd)
+        out.append(permute_bt(sd, facs[keys[k]]))
+    return out

@@ -1,0 +1,135 @@
+"""Python binding over the C ABI (include/sc.h): argument marshalling only.
+
+PyTorch provides device memory (caller-owned buffers) and streams; every step
+of the assembly and of the application runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _native, abi
+
+
+class SCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """sc_plan + the device buffers it needs (plan tables, workspace).
+
+    ``subdomains`` is a list of :class:`paper_2509_21037_gb300.host.FactoredSubdomain`
+    (L pattern, B^T in L's ordering, lambda map).
+    """
+
+    def __init__(self, subdomains: Sequence, n_dual: int):
+        self.lib = _native.sc_lib()
+        self.nsub = len(subdomains)
+        self.n_dual = int(n_dual)
+        keep: List[np.ndarray] = []       # arrays must outlive sc_plan
+        descs = (abi.SubdomainDesc * max(1, self.nsub))()
+        for i, fs in enumerate(subdomains):
+            arrs = [np.ascontiguousarray(fs.L.colptr, np.int64), np.ascontiguousarray(fs.L.rowind, np.int32),
+                    np.ascontiguousarray(fs.bt_colptr, np.int32), np.ascontiguousarray(fs.bt_rowind, np.int32),
+                    np.ascontiguousarray(fs.bt_sign, np.int8), np.ascontiguousarray(fs.lambda_map, np.int32)]
+            keep += arrs
+            d = descs[i]
+            d.n, d.m = fs.n, fs.m
+            d.L_colptr, d.L_rowind, d.Bt_colptr, d.Bt_rowind, d.Bt_sign, d.lambda_map = \
+                [a.ctypes.data if a.size else None for a in arrs]
+        h = ctypes.c_void_p()
+        opt = abi.Options()
+        st = self.lib.sc_plan(ctypes.byref(h), self.nsub, descs, self.n_dual, ctypes.byref(opt))
+        self.h = h
+        if st != abi.SC_OK:
+            msg = self.lib.sc_last_error(h).decode() if h.value else "sc_plan failed"
+            if h.value:
+                self.lib.sc_destroy(h)
+                self.h = ctypes.c_void_p()
+            raise SCError(st, msg)
+        self.sizes = abi.Sizes()
+        self._check(self.lib.sc_get_sizes(self.h, ctypes.byref(self.sizes)))
+        self.stats = abi.Stats()
+        self._check(self.lib.sc_get_stats(self.h, ctypes.byref(self.stats)))
+        self.F_offsets = np.zeros(self.nsub + 1, np.int64)
+        self.L_offsets = np.zeros(self.nsub + 1, np.int64)
+        self._check(self.lib.sc_get_offsets(self.h, self.F_offsets.ctypes.data, self.L_offsets.ctypes.data))
+        self.m = [fs.m for fs in subdomains]
+        self.n = [fs.n for fs in subdomains]
+        self.plan_dev = None
+        self.ws = None
+
+    # -- helpers
+    def _check(self, st: int):
+        if st != abi.SC_OK:
+            raise SCError(st, self.lib.sc_last_error(self.h).decode())
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                self.lib.sc_destroy(self.h)
+                self.h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+    # -- device side
+    def upload(self, device="cuda", stream=None):
+        import torch
+        self.plan_dev = torch.empty(max(1, self.sizes.plan_bytes), dtype=torch.uint8, device=device)
+        self._check(self.lib.sc_upload_plan(self.h, self.plan_dev.data_ptr(), self.plan_dev.numel(),
+                                            _stream_ptr(stream)))
+        self.ws = torch.empty(max(256, self.sizes.ws_bytes), dtype=torch.uint8, device=device)
+        return self
+
+    def new_F(self, device="cuda"):
+        import torch
+        return torch.empty(max(1, self.sizes.F_doubles), dtype=torch.float64, device=device)
+
+    def assemble(self, L_values, F, stream=None, ws=None):
+        ws = self.ws if ws is None else ws
+        self._check(self.lib.sc_assemble_batch(self.h, L_values.data_ptr(), F.data_ptr(), ws.data_ptr(),
+                                               ws.numel(), _stream_ptr(stream)))
+
+    def device_status(self, stream=None, ws=None) -> int:
+        ws = self.ws if ws is None else ws
+        return self.lib.sc_device_status(self.h, ws.data_ptr(), _stream_ptr(stream))
+
+    def apply(self, F, lam, q, stream=None):
+        self._check(self.lib.sc_apply(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(), _stream_ptr(stream)))
+
+    def export(self, F, i: int, dst=None, stream=None):
+        import torch
+        m = self.m[i]
+        if dst is None:
+            dst = torch.empty((m, m), dtype=torch.float64, device=F.device)
+        # column-major m x m with ld = m  ==  row-major transposed view
+        self._check(self.lib.sc_export_F(self.h, F.data_ptr(), i, dst.data_ptr(), max(1, m), _stream_ptr(stream)))
+        return dst.t()
+
+    def enable_stage_timing(self, on: bool = True):
+        self._check(self.lib.sc_enable_stage_timing(self.h, int(on)))
+
+    def stage_times(self):
+        """Elapsed ms of the last timed assembly: (prep, trsm, syrk)."""
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.sc_stage_times(self.h, ms, 3))
+        return tuple(float(x) for x in ms)
+
+    def stats_dict(self) -> dict:
+        return {k: getattr(self.stats, k) for k, _ in abi.Stats._fields_}
+
+
+def concat_L_values(subdomains) -> np.ndarray:
+    return np.concatenate([fs.L.values for fs in subdomains]) if subdomains else np.zeros(0)

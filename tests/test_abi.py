@@ -1,0 +1,210 @@
+"""CPU-side checks of the C ABI: the library loads and exports every declared
+symbol; sc_plan validates its inputs; the exported plan keeps every kernel
+address in bounds and, replayed on the CPU, reproduces the oracle's F."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2509_21037_gb300 import _native, abi, host, sc
+
+import plan_emulator as pe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(sc[A-Za-z_]*)\s*\(", src, flags=re.M))
+
+
+@pytest.mark.parametrize("header,loader", [("sc.h", _native.sc_lib), ("sc_dense.h", _native.dense_lib),
+                                           ("sc_factor.h", _native.factor_lib)])
+def test_library_exports_every_declared_symbol(header, loader):
+    names = _declared(header)
+    assert names, header
+    lib = loader()
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in {header} but not exported"
+
+
+def test_binding_covers_header():
+    assert _declared("sc.h") == set(abi.SC_SYMBOLS)
+    assert _declared("sc_dense.h") == set(abi.DENSE_SYMBOLS)
+
+
+def _plan_raw(descs, n_dual):
+    lib = _native.sc_lib()
+    h = ctypes.c_void_p()
+    arr = (abi.SubdomainDesc * max(1, len(descs)))(*descs)
+    st = lib.sc_plan(ctypes.byref(h), len(descs), arr, n_dual, None)
+    msg = lib.sc_last_error(h).decode() if h.value else ""
+    if h.value:
+        lib.sc_destroy(h)
+    return st, msg
+
+
+def _desc_from(fs, keep, **over):
+    arrs = dict(colptr=fs.L.colptr.copy(), rowind=fs.L.rowind.copy(), btc=fs.bt_colptr.copy(),
+                btr=fs.bt_rowind.copy(), sign=fs.bt_sign.copy(), lam=fs.lambda_map.copy())
+    arrs.update(over)
+    keep.append(arrs)
+    d = abi.SubdomainDesc()
+    d.n = over.get("n", fs.n)
+    d.m = over.get("m", fs.m)
+    d.L_colptr = arrs["colptr"].ctypes.data
+    d.L_rowind = arrs["rowind"].ctypes.data
+    d.Bt_colptr = arrs["btc"].ctypes.data
+    d.Bt_rowind = arrs["btr"].ctypes.data
+    d.Bt_sign = arrs["sign"].ctypes.data
+    d.lambda_map = arrs["lam"].ctypes.data
+    return d
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    prob = synth.make_config(1)
+    return prob, host.factorize_problem(prob.subdomains)
+
+
+def test_plan_accepts_valid(cfg1):
+    prob, fs = cfg1
+    keep = []
+    st, msg = _plan_raw([_desc_from(fs[0], keep)], prob.n_dual)
+    assert st == abi.SC_OK, msg
+
+
+@pytest.mark.parametrize("case", ["diag_not_first", "row_out_of_range", "bad_sign", "bt_unsorted",
+                                  "lambda_out_of_range", "negative_m"])
+def test_plan_rejects_invalid(cfg1, case):
+    prob, fs = cfg1
+    f = fs[0]
+    keep = []
+    if case == "diag_not_first":
+        ri = f.L.rowind.copy()
+        a = f.L.colptr[5]
+        ri[a], ri[a + 1] = ri[a + 1], ri[a]
+        d = _desc_from(f, keep, rowind=ri)
+    elif case == "row_out_of_range":
+        ri = f.L.rowind.copy()
+        ri[f.L.colptr[3] + 1] = f.n + 7
+        d = _desc_from(f, keep, rowind=ri)
+    elif case == "bad_sign":
+        sg = f.bt_sign.copy()
+        sg[0] = 2
+        d = _desc_from(f, keep, sign=sg)
+    elif case == "bt_unsorted":
+        # column 0 with two rows in descending order
+        btc = f.bt_colptr.copy()
+        btc[1:] += 1
+        btr = np.concatenate([[f.bt_rowind[0] + 1, f.bt_rowind[0]], f.bt_rowind[1:]]).astype(np.int32)
+        sg = np.concatenate([[1, 1], f.bt_sign[1:]]).astype(np.int8)
+        d = _desc_from(f, keep, btc=btc, btr=btr, sign=sg)
+    elif case == "lambda_out_of_range":
+        lam = f.lambda_map.copy()
+        lam[3] = prob.n_dual
+        d = _desc_from(f, keep, lam=lam)
+    else:
+        d = _desc_from(f, keep, m=-1)
+    st, msg = _plan_raw([d], prob.n_dual)
+    assert st == abi.SC_ERR_INVALID_ARG and msg
+
+
+def test_empty_batch_and_empty_subdomain():
+    st, _ = _plan_raw([], 0)
+    assert st == abi.SC_OK
+    d = abi.SubdomainDesc()
+    cp = np.array([0, 1, 2], np.int64)
+    ri = np.array([0, 1], np.int32)
+    btc = np.array([0], np.int32)
+    d.n, d.m = 2, 0
+    d.L_colptr, d.L_rowind, d.Bt_colptr = cp.ctypes.data, ri.ctypes.data, btc.ctypes.data
+    st, msg = _plan_raw([d], 0)
+    assert st == abi.SC_OK, msg
+
+
+def _cases():
+    yield "config1", synth.make_config(1)
+    yield "cube_2x5", synth.cube_heat_3d(2, 5)
+    yield "cube_coef", synth.cube_heat_3d(2, 3, coef_seed=4)
+    yield "elast", synth.elasticity_cubes((2, 1, 1), 2, 3, seed=1)
+
+
+@pytest.mark.parametrize("name,prob", list(_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_plan_emulation_matches_oracle(name, prob):
+    fs = host.factorize_problem(prob.subdomains)
+    plan = sc.Plan(fs, prob.n_dual)
+    T = pe.export_plan(plan)
+    pe.check_bounds(T, plan.sizes, plan.stats)
+    F = pe.emulate_assembly(T, plan.sizes, plan.stats, sc.concat_L_values(fs))
+    assert not np.isnan(F).any(), "F entries left unwritten"
+    Fo = oracle.dual_operators(prob.subdomains)
+    for i in range(len(fs)):
+        assert oracle.relative_frobenius(pe.export_dense(T, F, i), Fo[i]) <= 1e-12
+
+
+def _dense_factor_plan_stats(n, m):
+    """Plan counters for a dense lower factor (one supernode) with the
+    perfectly triangular right-hand side of paper Sec. 4.3: the pivot of
+    column i is row i n / m."""
+    cp = np.zeros(n + 1, np.int64)
+    cp[1:] = np.cumsum(n - np.arange(n))
+    ri = np.concatenate([np.arange(c, n) for c in range(n)]).astype(np.int32)
+    piv = ((np.arange(m) * n) // m).astype(np.int32)
+    btc = np.arange(m + 1, dtype=np.int32)
+    lam = np.arange(m, dtype=np.int32)
+    sg = np.ones(m, np.int8)
+    d = abi.SubdomainDesc()
+    d.n, d.m = n, m
+    d.L_colptr, d.L_rowind, d.Bt_colptr = cp.ctypes.data, ri.ctypes.data, btc.ctypes.data
+    d.Bt_rowind, d.Bt_sign, d.lambda_map = piv.ctypes.data, sg.ctypes.data, lam.ctypes.data
+    lib = _native.sc_lib()
+    h = ctypes.c_void_p()
+    assert lib.sc_plan(ctypes.byref(h), 1, ctypes.byref(d), m, None) == 0
+    s = abi.Stats()
+    lib.sc_get_stats(h, ctypes.byref(s))
+    lib.sc_destroy(h)
+    return s
+
+
+def test_perfect_triangle_flop_ratio():
+    """Paper Sec. 4.3: for a perfectly triangular RHS, dense TRSM and SYRK do 3x
+    the flops of the pivot-pruned ones (pyramid vs prism).  The plan's own
+    counters approach 3 as the 32-row blocks get small relative to n."""
+    ratios = []
+    for n, m in [(256, 128), (1024, 512), (2048, 1024)]:
+        s = _dense_factor_plan_stats(n, m)
+        assert s.n_supernodes == 1
+        ratios.append(s.flops_dense / (s.flops_trsm + s.flops_syrk))
+    assert ratios[0] < ratios[1] < ratios[2] < 3.0
+    assert ratios[2] > 2.85
+
+
+def test_perfect_triangle_emulation():
+    """The cut-trimmed plan still produces F exactly on a dense factor."""
+    rng = np.random.default_rng(3)
+    n, m = 150, 70
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)
+    G = np.linalg.cholesky(A)
+    cp = np.zeros(n + 1, np.int64)
+    cp[1:] = np.cumsum(n - np.arange(n))
+    ri = np.concatenate([np.arange(c, n) for c in range(n)]).astype(np.int32)
+    vals = np.concatenate([G[c:, c] for c in range(n)])
+    piv = ((np.arange(m) * n) // m).astype(np.int32)
+    sign = rng.choice([-1, 1], size=m).astype(np.int8)
+    L = host.HostFactor(n, cp, ri, vals, np.arange(n, dtype=np.int32))
+    fs = host.FactoredSubdomain(L, np.arange(m + 1, dtype=np.int32), piv, sign, np.arange(m, dtype=np.int32))
+    plan = sc.Plan([fs], m)
+    T = pe.export_plan(plan)
+    pe.check_bounds(T, plan.sizes, plan.stats)
+    F = pe.export_dense(T, pe.emulate_assembly(T, plan.sizes, plan.stats, vals), 0)
+    Bt = np.zeros((n, m))
+    Bt[piv, np.arange(m)] = sign
+    ref = Bt.T @ np.linalg.solve(A, Bt)
+    assert oracle.relative_frobenius(F, ref) < 1e-12
