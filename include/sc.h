@@ -158,6 +158,32 @@ sc_status sc_upload_plan(sc_ctx *ctx, void *plan_dev, size_t plan_bytes, void *s
 sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_dev,
                             void *ws_dev, size_t ws_bytes, void *stream);
 
+/* Size of the library-owned scratch used by sc_assemble_batch_static. */
+#define SC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* Batched assembly that allocates nothing: like sc_assemble_batch, but the
+ * workspace is a 64 MiB array inside the library (SC_STATIC_SCRATCH_BYTES)
+ * instead of caller memory.  The paper has no counterpart; this entry point
+ * exists for callers that cannot call cudaMalloc -- a solver whose memory
+ * manager reserved the free device memory up front, or a latency-sensitive
+ * loop that cannot afford cudaMalloc's implicit device-wide synchronisation.
+ * The caller still passes the inputs and outputs: the uploaded plan
+ * (sc_upload_plan), L_values_dev and F_dev, as for sc_assemble_batch.
+ *   - Plans whose sizes.ws_bytes exceeds SC_STATIC_SCRATCH_BYTES are rejected
+ *     with SC_ERR_OOM before anything is launched.
+ *   - The array is allocated on every device that loads the library's module
+ *     and stays allocated until the process exits.
+ *   - The first call on a device looks up the array's device address (set-up,
+ *     done once per device with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents: calls that overlap on the GPU (other streams, other
+ *     threads, other contexts) race and must be serialised by the caller.
+ *   - The call synchronises `stream` and returns this call's device status
+ *     (SC_OK or SC_ERR_NOT_SPD), so no sc_device_status call is needed.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_values_dev, double *F_dev, void *stream);
+
 /* Synchronises `stream` and reads the device status word in ws_dev:
  * SC_OK, or SC_ERR_NOT_SPD when a diagonal of L was not positive and finite. */
 sc_status sc_device_status(sc_ctx *ctx, const void *ws_dev, void *stream);

@@ -46,6 +46,7 @@ SC_SYMBOLS = {
     "sc_upload_plan": ([c_vp, c_vp, c_sz, c_vp], c_int),
     "sc_assemble_batch": ([c_vp, c_vp, c_vp, c_vp, c_sz, c_vp], c_int),
     "sc_device_status": ([c_vp, c_vp, c_vp], c_int),
+    "sc_assemble_batch_static": ([c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_export_F": ([c_vp, c_vp, c_i32, c_vp, c_i32, c_vp], c_int),
     "sc_enable_stage_timing": ([c_vp, c_i32], c_int),
