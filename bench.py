@@ -245,6 +245,12 @@ def run_sc(args):
     nsub = len(fs)
     value = world * nsub / (ms / 1e3)
 
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "stage_ms": {
+                "trsm": sum(trsm_ms) / len(trsm_ms), "syrk": sum(syrk_ms) / len(syrk_ms)}}))
+        return 0
+
     # end to end through the public API from pinned host buffers
     Lpin = torch.from_numpy(Lh).pin_memory()
     lam_pin = lam.cpu().pin_memory()
@@ -348,6 +354,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-dense", dest="dense", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile", action="store_true",
+                    help="device steps only (no e2e, comparator or CPU baseline): for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
