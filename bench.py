@@ -281,6 +281,28 @@ def run_sc(args):
     if plan.device_status(stream) != 0:
         raise RuntimeError("device status not OK after the timed steps")
 
+    # amortisation point (paper Sec. 1 and Sec. 5): iterations after which the
+    # explicit operator (assembly + cheap applies) beats the implicit one (no
+    # assembly, sparse triangular solves every iteration); the numeric
+    # factorisation is common to both and cancels
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(20):
+        plan.apply(F, lam, q, stream)
+    a1.record(stream)
+    a1.synchronize()
+    t_expl = a0.elapsed_time(a1) / 20
+    impl = host.ImplicitApply(fs, prob.n_dual)
+    lam_h = lam.cpu().numpy()
+    impl(lam_h)
+    t_impl = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        impl(lam_h)
+        t_impl.append(1e3 * (time.perf_counter() - t0))
+    t_impl = statistics.median(t_impl)
+    t_asm = sum(prep_ms) / len(prep_ms) + sum(trsm_ms) / len(trsm_ms) + sum(syrk_ms) / len(syrk_ms)
+
     # dominant kernel roofline (FP64 pipe)
     syrk_avg = sum(syrk_ms) / len(syrk_ms)
     trsm_avg = sum(trsm_ms) / len(trsm_ms)
@@ -304,6 +326,11 @@ def run_sc(args):
         "e2e": {"value": world * nsub / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(Lpin.numel() * 8 + lam_pin.numel() * 8),
                 "d2h_bytes_per_step": int(q_pin.numel() * 8)},
+        "amortization": {"iterations": t_asm / (t_impl - t_expl) if t_impl > t_expl else None,
+                         "iterations_incl_L_h2d": (t_asm + (e2e_ms - ms)) / (t_impl - t_expl)
+                         if t_impl > t_expl else None,
+                         "t_assembly_ms": t_asm, "t_apply_explicit_gpu_ms": t_expl,
+                         "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count()},
         "gpu_launches": args.steps * 5,
         "clocks": clocks.summary(),
     }

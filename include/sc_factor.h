@@ -46,6 +46,27 @@ int scf_export(const scf_factor *f, int64_t *colptr, int32_t *rowind, double *va
 
 void scf_free(scf_factor *f);
 
+/* Implicit application of the dual operator on the host (paper Sec. 2.2,
+ * Eq. "dualop_apply_impl"): q = sum_i B_i L_i^{-T} L_i^{-1} B_i^T lambda_i,
+ * i.e. a sparse scatter, two sparse triangular solves and a sparse gather per
+ * subdomain.  Arrays as in sc_subdomain_desc plus L's values; all host memory,
+ * read only; q (n_dual doubles) is overwritten.  nthreads <= 0 uses every
+ * hardware thread; threads split the subdomains and sum private dual vectors
+ * in a fixed order.  Returns SCF_ERR_INVALID_ARG on bad sizes or maps. */
+typedef struct {
+  int32_t n, m;
+  const int64_t *L_colptr;
+  const int32_t *L_rowind;
+  const double *L_val;
+  const int32_t *Bt_colptr;
+  const int32_t *Bt_rowind;
+  const int8_t *Bt_sign;
+  const int32_t *lambda_map;
+} scf_apply_subdomain;
+
+int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, const double *lambda,
+                       double *q, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

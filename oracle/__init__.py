@@ -42,7 +42,7 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = ["regularize", "cholesky", "forward_substitution", "backward_substitution",
-           "solve_spd", "dual_operator", "dual_operators", "apply_dual",
+           "solve_spd", "dual_operator", "dual_operator_columns", "dual_operators", "apply_dual",
            "relative_frobenius", "NotSPDError"]
 
 
@@ -182,6 +182,17 @@ def dual_operator(sd, memo: Optional[_Memo] = None) -> np.ndarray:
     Xd = _columns(sd, dofs, memo)                       # n x |dofs|
     # X = K_reg^{-1} B^T = Xd @ Bt[dofs, :]
     X = Xd @ Bt[dofs, :].toarray()
+    return np.asarray(Bt.T @ X)
+
+
+def dual_operator_columns(sd, cols: Sequence[int], memo: Optional[_Memo] = None) -> np.ndarray:
+    """F[:, cols] = B K_reg^{-1} B^T[:, cols] (m x len(cols)): the same definition
+    restricted to selected columns, for spot checks of large subdomains."""
+    Bt = sp.csc_matrix(sd.Bt)
+    sub = Bt[:, list(cols)]
+    dofs = np.unique(sub.indices)
+    Xd = _columns(sd, dofs, memo)
+    X = Xd @ sub[dofs, :].toarray()
     return np.asarray(Bt.T @ X)
 
 

@@ -66,7 +66,8 @@ def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
     o_dense = os.path.join(OBJ, "sc_dense.cu.o")
     cmds.append(_nvcc_obj(os.path.join(CSRC, "sc_dense.cu"), o_dense, list(extra_nvcc)))
     cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-I", INC,
-                 os.path.join(CSRC, "host_factor.cpp"), "-o", os.path.join(OUT, "libscfactor.so")])
+                 os.path.join(CSRC, "host_factor.cpp"), os.path.join(CSRC, "host_apply.cpp"), "-pthread",
+                 "-o", os.path.join(OUT, "libscfactor.so")])
     if verbose:
         for c in cmds:
             print(" ".join(c), file=sys.stderr)

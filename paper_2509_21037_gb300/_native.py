@@ -42,6 +42,8 @@ def factor_lib() -> ctypes.CDLL:
         lib.scf_export.restype = c_int
         lib.scf_free.argtypes = [c_vp]
         lib.scf_free.restype = None
+        lib.scf_implicit_apply.argtypes = [c_i32, c_vp, c_i64, c_vp, c_vp, c_i32]
+        lib.scf_implicit_apply.restype = c_int
         lib._typed = True
     return lib
 

@@ -151,6 +151,43 @@ def permute_bt(sd, L: HostFactor) -> FactoredSubdomain:
     return FactoredSubdomain(L, cp, ri, sg, np.asarray(sd.lambda_map, np.int32))
 
 
+class _ApplySub(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("L_colptr", ctypes.c_void_p),
+                ("L_rowind", ctypes.c_void_p), ("L_val", ctypes.c_void_p), ("Bt_colptr", ctypes.c_void_p),
+                ("Bt_rowind", ctypes.c_void_p), ("Bt_sign", ctypes.c_void_p), ("lambda_map", ctypes.c_void_p)]
+
+
+class ImplicitApply:
+    """Host implicit application q = sum_i B_i L_i^-T L_i^-1 B_i^T lambda_i
+    (paper Eq. "dualop_apply_impl"), the per-iteration alternative to the
+    explicit F*lambda."""
+
+    def __init__(self, subdomains: Sequence[FactoredSubdomain], n_dual: int):
+        self.lib = _native.factor_lib()
+        self.n_dual = int(n_dual)
+        self._keep = []
+        self.arr = (_ApplySub * max(1, len(subdomains)))()
+        for i, fs in enumerate(subdomains):
+            a = [np.ascontiguousarray(fs.L.colptr, np.int64), np.ascontiguousarray(fs.L.rowind, np.int32),
+                 np.ascontiguousarray(fs.L.values, np.float64), np.ascontiguousarray(fs.bt_colptr, np.int32),
+                 np.ascontiguousarray(fs.bt_rowind, np.int32), np.ascontiguousarray(fs.bt_sign, np.int8),
+                 np.ascontiguousarray(fs.lambda_map, np.int32)]
+            self._keep += a
+            s = self.arr[i]
+            s.n, s.m = fs.n, fs.m
+            s.L_colptr, s.L_rowind, s.L_val, s.Bt_colptr, s.Bt_rowind, s.Bt_sign, s.lambda_map = \
+                [x.ctypes.data if x.size else None for x in a]
+        self.nsub = len(subdomains)
+
+    def __call__(self, lam: np.ndarray, threads: int = 0) -> np.ndarray:
+        lam = np.ascontiguousarray(lam, np.float64)
+        q = np.empty(self.n_dual)
+        rc = self.lib.scf_implicit_apply(self.nsub, self.arr, self.n_dual, lam.ctypes.data, q.ctypes.data, threads)
+        if rc != 0:
+            raise RuntimeError(f"scf_implicit_apply failed ({rc})")
+        return q
+
+
 def factorize_problem(subdomains, threads: int = 0, leaf: int = 8) -> List[FactoredSubdomain]:
     """Order and factorise every subdomain (identical keys factorised once)."""
     keys: Dict[object, int] = {}

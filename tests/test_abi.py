@@ -208,3 +208,14 @@ def test_perfect_triangle_emulation():
     Bt[piv, np.arange(m)] = sign
     ref = Bt.T @ np.linalg.solve(A, Bt)
     assert oracle.relative_frobenius(F, ref) < 1e-12
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_host_implicit_apply_matches_oracle(threads):
+    prob = synth.cube_heat_3d(2, 4, coef_seed=2)
+    fs = host.factorize_problem(prob.subdomains)
+    lam = np.random.default_rng(9).standard_normal(prob.n_dual)
+    q = host.ImplicitApply(fs, prob.n_dual)(lam, threads=threads)
+    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains), [s.lambda_map for s in prob.subdomains],
+                           lam, prob.n_dual)
+    assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)

@@ -198,3 +198,52 @@ def test_dense_comparator_matches_oracle(dev):
     Fd = dense.assemble_dense(fs, dev, emulation=0)
     Fo = oracle.dual_operators(prob.subdomains)
     assert oracle.relative_frobenius(Fd[0], Fo[0]) <= TOL
+
+
+def test_cuda_graph_capture_replay(dev):
+    """sc_assemble_batch + sc_apply captured in one CUDA graph and replayed."""
+    prob = synth.cube_heat_3d(parts=2, k=6, coef_seed=1)
+    fs = host.factorize_problem(prob.subdomains)
+    plan, F_ref, Lv = _assemble(fs, prob.n_dual, dev)
+    lam = torch.from_numpy(np.random.default_rng(4).standard_normal(prob.n_dual)).to(dev)
+    q_ref = torch.empty_like(lam)
+    plan.apply(F_ref, lam, q_ref)
+    F = plan.new_F(dev)
+    q = torch.empty_like(lam)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.assemble(Lv, F, stream=s)
+            plan.apply(F, lam, q, stream=s)
+    for _ in range(3):
+        F.fill_(float("nan"))
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(F, F_ref)
+    assert torch.allclose(q, q_ref, rtol=1e-13, atol=1e-13)
+
+
+def test_config3_full_size_sampled(dev):
+    """Config 3 (512 uneven elasticity cubes, k in 8..16) assembled in one
+    batch; the subdomains of the smallest edge length are compared in full,
+    those of the largest on sampled columns (the oracle is dense)."""
+    prob = synth.make_config(3)
+    fs = host.factorize_problem(prob.subdomains, threads=0)
+    plan, F, _ = _assemble(fs, prob.n_dual, dev)
+    ks = [round((s.n // 3) ** (1 / 3)) - 1 for s in prob.subdomains]
+    memo = oracle._Memo()
+    small = [i for i, k in enumerate(ks) if k == min(ks)][:3]
+    big = [i for i, k in enumerate(ks) if k == max(ks)][:2]
+    for i in small:
+        Fo = oracle.dual_operator(prob.subdomains[i], memo)
+        assert oracle.relative_frobenius(plan.export(F, i).cpu().numpy(), Fo) <= TOL
+    rng = np.random.default_rng(0)
+    for i in big:
+        sd = prob.subdomains[i]
+        cols = sorted(rng.choice(sd.m, size=24, replace=False).tolist())
+        Fo = oracle.dual_operator_columns(sd, cols, memo)
+        Fg = plan.export(F, i).cpu().numpy()[:, cols]
+        assert oracle.relative_frobenius(Fg, Fo) <= TOL

@@ -175,6 +175,12 @@ def test_coefficient_scaling():
         assert np.allclose(Fs[np.ix_(fixed, fixed)], Fu[np.ix_(fixed, fixed)], atol=1e-15)
 
 
+def test_sampled_columns_against_brute_force():
+    sd = synth.elasticity_cubes((2, 1, 1), 2, 3, seed=4).subdomains[1]
+    cols = [0, 5, sd.m - 1]
+    assert oracle.relative_frobenius(oracle.dual_operator_columns(sd, cols), _brute(sd)[:, cols]) < 1e-12
+
+
 def test_apply_dual_sums_subdomains():
     p = synth.cube_heat_3d(parts=2, k=2)
     Fs = oracle.dual_operators(p.subdomains)
