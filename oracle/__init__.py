@@ -20,6 +20,11 @@ in FP64, by
   3. ``solve_spd``    -- forward then backward substitution with G on the
                          distinct dofs touched by B^T;
   4. ``dual_operator``-- F = B X, returned as a full symmetric m x m matrix;
+                         optionally after iterative refinement of X with an
+                         error-free residual (``refine`` steps), because for
+                         floating subdomains fixed at few dofs kappa(K_reg)
+                         reaches 1e6 and a plain FP64 solve is then only good
+                         to ~1e-12;
   5. ``apply_dual``   -- q = sum_i scatter_i(F_i gather_i(lambda))
                          (paper Eq. "dualop_apply_expl" summed over subdomains).
 
@@ -41,7 +46,7 @@ from typing import Dict, Iterable, List, Optional, Sequence
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["regularize", "cholesky", "forward_substitution", "backward_substitution",
+__all__ = ["regularize", "regularized_sparse", "residual", "cholesky", "forward_substitution", "backward_substitution",
            "solve_spd", "dual_operator", "dual_operator_columns", "dual_operators", "apply_dual",
            "relative_frobenius", "NotSPDError"]
 
@@ -141,6 +146,61 @@ def solve_spd(G: np.ndarray, R: np.ndarray) -> np.ndarray:
     return backward_substitution(G, forward_substitution(G, R))
 
 
+# ---------------------------------------------------------------------------
+# error-free transformations (Dekker 1971; Knuth TAOCP vol. 2, Sec. 4.2.2)
+
+_SPLIT = 134217729.0   # 2^27 + 1
+
+
+def _two_prod(a: np.ndarray, b: np.ndarray):
+    """p + e == a * b exactly (Dekker's product, Veltkamp splitting)."""
+    p = a * b
+    t = _SPLIT * a
+    ah = t - (t - a)
+    al = a - ah
+    t = _SPLIT * b
+    bh = t - (t - b)
+    bl = b - bh
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def _two_sum(a: np.ndarray, b: np.ndarray):
+    """s + e == a + b exactly (Knuth's two-sum)."""
+    s = a + b
+    bb = s - a
+    e = (a - (s - bb)) + (b - bb)
+    return s, e
+
+
+def regularized_sparse(K: sp.spmatrix, fixed: Sequence[int]) -> sp.csr_matrix:
+    """Sparse K_reg, same definition as ``regularize``."""
+    A = sp.lil_matrix(K, dtype=np.float64)
+    for f in fixed:
+        A[f, :] = 0.0
+        A[:, f] = 0.0
+        A[f, f] = 1.0
+    return A.tocsr()
+
+
+def residual(A: sp.csr_matrix, X: np.ndarray, R0: np.ndarray) -> np.ndarray:
+    """R0 - A X with every product and sum carried in double-double, rounded
+    once at the end (A sparse)."""
+    A = sp.csr_matrix(A)
+    hi = np.array(R0, dtype=np.float64, copy=True)
+    lo = np.zeros_like(hi)
+    cnt = np.diff(A.indptr)
+    for j in range(int(cnt.max()) if len(cnt) else 0):
+        rows = np.nonzero(cnt > j)[0]
+        idx = A.indptr[rows] + j
+        a = -A.data[idx][:, None] * np.ones((1, X.shape[1]))
+        p, pe = _two_prod(a, X[A.indices[idx]])
+        s, se = _two_sum(hi[rows], p)
+        hi[rows] = s
+        lo[rows] += se + pe
+    return hi + lo
+
+
 class _Memo:
     """Per-K cache of the factor and of solved unit columns K_reg^{-1} e_d."""
 
@@ -149,57 +209,68 @@ class _Memo:
         self.cols: Dict[tuple, Dict[int, np.ndarray]] = {}
 
 
-def _columns(sd, dofs: np.ndarray, memo: Optional[_Memo]) -> np.ndarray:
+def _solve_unit_columns(sd, G: np.ndarray, dofs, refine: int) -> np.ndarray:
+    """K_reg^{-1}[:, dofs]: forward/backward substitution, then ``refine``
+    steps X += K_reg^{-1}(E - K_reg X) with the residual formed exactly."""
+    E = np.zeros((sd.n, len(dofs)))
+    E[list(dofs), np.arange(len(dofs))] = 1.0
+    X = solve_spd(G, E)
+    if refine:
+        A = regularized_sparse(sd.K, sd.fixed)
+        for _ in range(refine):
+            X = X + solve_spd(G, residual(A, X, E))
+    return X
+
+
+def _columns(sd, dofs: np.ndarray, memo: Optional[_Memo], refine: int = 0) -> np.ndarray:
     """K_reg^{-1}[:, dofs] for the subdomain, reusing memoised columns."""
     key = getattr(sd, "key", None) if memo is not None else None
     if key is None:
-        G = cholesky(regularize(sd.K, sd.fixed))
-        E = np.zeros((sd.n, len(dofs)))
-        E[dofs, np.arange(len(dofs))] = 1.0
-        return solve_spd(G, E)
+        return _solve_unit_columns(sd, cholesky(regularize(sd.K, sd.fixed)), dofs, refine)
+    key = (key, refine)
     if key not in memo.G:
         memo.G[key] = cholesky(regularize(sd.K, sd.fixed))
         memo.cols[key] = {}
     have = memo.cols[key]
     need = [int(d) for d in dofs if int(d) not in have]
     if need:
-        E = np.zeros((sd.n, len(need)))
-        E[need, np.arange(len(need))] = 1.0
-        X = solve_spd(memo.G[key], E)
+        X = _solve_unit_columns(sd, memo.G[key], need, refine)
         for c, d in enumerate(need):
             have[d] = X[:, c]
     return np.stack([have[int(d)] for d in dofs], axis=1)
 
 
-def dual_operator(sd, memo: Optional[_Memo] = None) -> np.ndarray:
+def dual_operator(sd, memo: Optional[_Memo] = None, refine: int = 0) -> np.ndarray:
     """F = B K_reg^{-1} B^T (m x m, full symmetric), paper Eq. "localdualoperator".
 
     B^T may have any number of nonzeros per column; X = K_reg^{-1} B^T is
-    formed from the unit columns of the distinct dofs B^T touches.
+    formed from the unit columns of the distinct dofs B^T touches, with
+    ``refine`` steps of iterative refinement.
     """
     Bt = sp.csc_matrix(sd.Bt)
     dofs = np.unique(Bt.indices)
-    Xd = _columns(sd, dofs, memo)                       # n x |dofs|
+    Xd = _columns(sd, dofs, memo, refine)               # n x |dofs|
     # X = K_reg^{-1} B^T = Xd @ Bt[dofs, :]
     X = Xd @ Bt[dofs, :].toarray()
     return np.asarray(Bt.T @ X)
 
 
-def dual_operator_columns(sd, cols: Sequence[int], memo: Optional[_Memo] = None) -> np.ndarray:
+def dual_operator_columns(sd, cols: Sequence[int], memo: Optional[_Memo] = None,
+                          refine: int = 0) -> np.ndarray:
     """F[:, cols] = B K_reg^{-1} B^T[:, cols] (m x len(cols)): the same definition
     restricted to selected columns, for spot checks of large subdomains."""
     Bt = sp.csc_matrix(sd.Bt)
     sub = Bt[:, list(cols)]
     dofs = np.unique(sub.indices)
-    Xd = _columns(sd, dofs, memo)
+    Xd = _columns(sd, dofs, memo, refine)
     X = Xd @ sub[dofs, :].toarray()
     return np.asarray(Bt.T @ X)
 
 
-def dual_operators(subdomains: Iterable, memo: Optional[_Memo] = None) -> List[np.ndarray]:
+def dual_operators(subdomains: Iterable, memo: Optional[_Memo] = None, refine: int = 0) -> List[np.ndarray]:
     """F_i for every subdomain, sharing K_reg^{-1} columns between equal keys."""
     memo = _Memo() if memo is None else memo
-    return [dual_operator(sd, memo) for sd in subdomains]
+    return [dual_operator(sd, memo, refine) for sd in subdomains]
 
 
 def apply_dual(Fs: Sequence[np.ndarray], lambda_maps: Sequence[np.ndarray], lam: np.ndarray,

@@ -66,6 +66,35 @@ def test_chain_closed_form(nel):
     assert np.max(np.abs(F - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
 
 
+def test_refinement_reaches_closed_form_on_ill_conditioned_chain():
+    """A long chain (kappa(K_reg) ~ 1e7): the plain FP64 solve misses the
+    closed form h*min(i,j) by ~1e-10; one refinement step with the exact
+    residual recovers it to ~1e-15 relative."""
+    nel = 3000
+    sel = np.array([1, 17, 700, 1500, 2999, 3000])
+    sd = synth.chain_1d(nel, sel)
+    h = 1.0 / nel
+    ref = h * np.minimum.outer(sel, sel).astype(float)
+    e0 = oracle.relative_frobenius(oracle.dual_operator(sd, refine=0), ref)
+    e1 = oracle.relative_frobenius(oracle.dual_operator(sd, refine=1), ref)
+    assert e1 <= 1e-14 and e1 < e0
+
+
+def test_residual_is_exact_against_rationals():
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    A = sp.random(12, 12, density=0.4, random_state=3, format="csr") + sp.eye(12)
+    A.data = rng.standard_normal(A.nnz) * 10.0 ** rng.integers(-8, 8, A.nnz)
+    X = rng.standard_normal((12, 3)) * 10.0 ** rng.integers(-8, 8, (12, 3))
+    R0 = rng.standard_normal((12, 3))
+    got = oracle.residual(A, X, R0)
+    Ad = A.toarray()
+    for i in range(12):
+        for c in range(3):
+            exact = Fraction(R0[i, c]) - sum(Fraction(Ad[i, k]) * Fraction(X[k, c]) for k in range(12))
+            assert abs(got[i, c] - float(exact)) <= np.spacing(abs(float(exact)))   # within one ulp of exact
+
+
 # ---------------------------------------------------------------- brute force
 
 def _tiny_cases():
