@@ -90,11 +90,22 @@ typedef struct {
   const int32_t *lambda_map;
 } sc_subdomain_desc;
 
-enum { SC_FP64 = 0 };
+enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
 
+/* precision: SC_FP64 -- every flop in IEEE binary64 (the default);
+ *            SC_SPLIT_BF16 -- the off-diagonal GEMM work (the SYRK Y^T Y
+ *            blocks and the TRSM updates below the diagonal triangles) runs
+ *            on the tensor cores as exact products of 8-bit digit planes of
+ *            the FP64 operands (BF16 in, FP32 accumulate, integer and FP64
+ *            combination), n_slices digits per operand; the diagonal-triangle
+ *            solves and the accumulation into Y and F stay FP64.  The error
+ *            is below about 2^(-8 n_slices) relative to the product of the
+ *            operands' column bounds; n_slices = 7 keeps 56 bits.
+ * n_slices: 3..7 for SC_SPLIT_BF16 (0 selects 7); ignored for SC_FP64. */
 typedef struct {
-  int32_t precision;   /* SC_FP64 */
-  int32_t reserved[7]; /* must be zero */
+  int32_t precision;
+  int32_t n_slices;
+  int32_t reserved[6]; /* must be zero */
 } sc_options;
 
 typedef struct {

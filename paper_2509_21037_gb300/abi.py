@@ -20,8 +20,11 @@ class SubdomainDesc(ctypes.Structure):
                 ("Bt_colptr", c_vp), ("Bt_rowind", c_vp), ("Bt_sign", c_vp), ("lambda_map", c_vp)]
 
 
+SC_FP64, SC_SPLIT_BF16 = 0, 1
+
+
 class Options(ctypes.Structure):
-    _fields_ = [("precision", c_i32), ("reserved", c_i32 * 7)]
+    _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("reserved", c_i32 * 6)]
 
 
 class Sizes(ctypes.Structure):

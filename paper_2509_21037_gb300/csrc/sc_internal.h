@@ -116,6 +116,8 @@ struct WsLayout {
 
 struct sc_ctx {
   std::string err;
+  int32_t precision = SC_FP64;
+  int32_t n_slices = 0;
   int32_t nsub = 0;
   int64_t n_dual = 0;
   std::vector<uint8_t> blob;     // plan tables, 256-byte aligned sections
@@ -146,6 +148,7 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
                 void *stream);
 int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, double *Y, void *stream);
 int launch_syrk(const sc_ctx &c, const double *Y, double *F, void *stream);
+int launch_syrk_split(const sc_ctx &c, const double *Y, double *F, void *stream);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);
 

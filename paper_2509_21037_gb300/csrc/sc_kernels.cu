@@ -266,6 +266,7 @@ int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, double *Y
 }
 
 int launch_syrk(const sc_ctx &c, const double *Y, double *F, void *stream) {
+  if (c.precision == SC_SPLIT_BF16) return launch_syrk_split(c, Y, F, stream);
   if (c.n_syrk > 0) syrk_kernel<<<(unsigned)c.n_syrk, kThreads, 0, S(stream)>>>(c.ptrs(), Y, F);
   return (int)cudaGetLastError();
 }

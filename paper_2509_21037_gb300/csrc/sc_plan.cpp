@@ -501,9 +501,16 @@ sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomain
   sc_status st = SC_OK;
   if (nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0) {
     st = fail(ctx, SC_ERR_INVALID_ARG, "nsub < 0, NULL subdomain array or n_dual < 0");
-  } else if (opt && opt->precision != SC_FP64) {
+  } else if (opt && opt->precision != SC_FP64 && opt->precision != SC_SPLIT_BF16) {
     st = fail(ctx, SC_ERR_INVALID_ARG, "unsupported precision");
+  } else if (opt && opt->precision == SC_SPLIT_BF16 && opt->n_slices != 0 &&
+             (opt->n_slices < 3 || opt->n_slices > 7)) {
+    st = fail(ctx, SC_ERR_INVALID_ARG, "n_slices must be 3..7 (or 0 for 7)");
   } else {
+    if (opt) {
+      ctx->precision = opt->precision;
+      ctx->n_slices = opt->precision == SC_SPLIT_BF16 ? (opt->n_slices ? opt->n_slices : 7) : 0;
+    }
     ctx->nsub = nsub;
     ctx->n_dual = n_dual;
     try {

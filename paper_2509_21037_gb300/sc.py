@@ -34,7 +34,7 @@ class Plan:
     (L pattern, B^T in L's ordering, lambda map).
     """
 
-    def __init__(self, subdomains: Sequence, n_dual: int):
+    def __init__(self, subdomains: Sequence, n_dual: int, precision: int = abi.SC_FP64, n_slices: int = 0):
         self.lib = _native.sc_lib()
         self.nsub = len(subdomains)
         self.n_dual = int(n_dual)
@@ -51,6 +51,8 @@ class Plan:
                 [a.ctypes.data if a.size else None for a in arrs]
         h = ctypes.c_void_p()
         opt = abi.Options()
+        opt.precision = precision
+        opt.n_slices = n_slices
         st = self.lib.sc_plan(ctypes.byref(h), self.nsub, descs, self.n_dual, ctypes.byref(opt))
         self.h = h
         if st != abi.SC_OK:

@@ -1,0 +1,52 @@
+"""Split-precision path (SC_SPLIT_BF16): error against the refined FP64 oracle
+as a function of the number of 8-bit digits per operand, reported and bounded.
+
+Each digit adds 8 bits, so the error must fall by roughly 2^-8 per extra slice
+until it reaches the FP64 input floor; with 7 digits (56 bits) it must meet
+the FP64 path's 1e-12 bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2509_21037_gb300 import abi, host, sc
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _errors(prob, dev, slices):
+    fs = host.factorize_problem(prob.subdomains)
+    Fo = oracle.dual_operators(prob.subdomains, refine=1)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    out = {}
+    for s in slices:
+        prec = abi.SC_FP64 if s == 0 else abi.SC_SPLIT_BF16
+        plan = sc.Plan(fs, prob.n_dual, precision=prec, n_slices=s).upload(dev)
+        F = plan.new_F(dev)
+        F.fill_(float("nan"))
+        plan.assemble(Lv, F)
+        assert plan.device_status() == abi.SC_OK
+        out[s] = max(oracle.relative_frobenius(plan.export(F, i).cpu().numpy(), Fo[i]) for i in range(plan.nsub))
+    return out
+
+
+@pytest.mark.parametrize("name", ["heat_cubes", "elasticity"])
+def test_split_error_by_slices(dev, name):
+    prob = synth.cube_heat_3d(parts=2, k=6, coef_seed=5) if name == "heat_cubes" else \
+        synth.elasticity_cubes((2, 2, 1), 3, 6, seed=4)
+    err = _errors(prob, dev, [0, 3, 4, 5, 6, 7])
+    print(name, {k: f"{v:.2e}" for k, v in err.items()})
+    assert err[0] <= 1e-12
+    assert err[7] <= 1e-12
+    for s in (3, 4, 5, 6):
+        assert err[s] <= 2.0 ** (-8 * s) * 1e3          # ~2^-8S times a modest growth factor
+        assert err[s] >= err[s + 1] or err[s + 1] <= 2 * err[0]
