@@ -195,7 +195,11 @@ def run_sc(args):
 
     prob = synth.make_config(2, seed=args.seed)
     fs = host.factorize_problem(prob.subdomains)
-    plan = sc.Plan(fs, prob.n_dual).upload(dev)
+    if args.profile and args.profile_slices:
+        from paper_2509_21037_gb300 import abi
+        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=args.profile_slices).upload(dev)
+    else:
+        plan = sc.Plan(fs, prob.n_dual).upload(dev)
     Lh = sc.concat_L_values(fs)
     Lv = torch.from_numpy(Lh).to(dev)
     F = plan.new_F(dev)
@@ -334,6 +338,8 @@ def run_sc(args):
         "gpu_launches": args.steps * 5,
         "clocks": clocks.summary(),
     }
+    if args.split and rank == 0:
+        line["split_precision"] = _split_section(args, fs, prob, Lv, lam, flush, stream, dev, ms)
     if args.dense and rank == 0:
         from paper_2509_21037_gb300 import dense
         del flush
@@ -371,6 +377,54 @@ def run_sc(args):
     return 0
 
 
+def _split_section(args, fs, prob, Lv, lam, flush, stream, dev, fp64_ms):
+    """The same workload with the off-diagonal GEMM work on the tensor cores
+    (SC_SPLIT_BF16), per number of 8-bit digit slices: throughput and the
+    per-subdomain relative Frobenius error against the refined FP64 oracle."""
+    import torch
+
+    import oracle
+    from paper_2509_21037_gb300 import abi, sc
+    Fo = oracle.dual_operators(prob.subdomains, refine=1) if args.split_error else None
+    out = {}
+    for S in args.split_slices:
+        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=S).upload(dev)
+        F = plan.new_F(dev)
+        q = torch.empty_like(lam)
+        for _ in range(args.warmup):
+            plan.assemble(Lv, F, stream)
+            plan.apply(F, lam, q, stream)
+        torch.cuda.synchronize(dev)
+        if plan.device_status(stream) != 0:
+            raise RuntimeError("device status not OK (split)")
+        plan.enable_stage_timing(True)
+        tot, trsm, syrk = [], [], []
+        for _ in range(args.steps):
+            flush.fill_(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.assemble(Lv, F, stream)
+            plan.apply(F, lam, q, stream)
+            b.record(stream)
+            _, tm, sy = plan.stage_times()
+            b.synchronize()
+            tot.append(a.elapsed_time(b)); trsm.append(tm); syrk.append(sy)
+        plan.enable_stage_timing(False)
+        ms = sum(tot) / len(tot)
+        st = plan.stats_dict()
+        rec = {"ms_per_step": ms, "assemblies_per_s": len(fs) / (ms / 1e3),
+               "speedup_vs_fp64_path": fp64_ms / ms,
+               "stage_ms": {"trsm": sum(trsm) / len(trsm), "syrk": sum(syrk) / len(syrk)},
+               "tensor_products_per_fp64_product": S * (S + 1) // 2,
+               "useful_fp64_equivalent_tflops": (st["flops_trsm"] + st["flops_syrk"]) / (ms / 1e3) / 1e12}
+        if Fo is not None:
+            errs = [oracle.relative_frobenius(plan.export(F, i).cpu().numpy(), Fo[i]) for i in range(len(fs))]
+            rec["rel_frobenius_error"] = {"max": max(errs), "median": float(np.median(errs)), "min": min(errs)}
+        out[f"slices_{S}"] = rec
+        del plan, F
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,6 +435,12 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-dense", dest="dense", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-split", dest="split", action="store_false",
+                    help="skip the split-precision (tensor-core) variant of the workload")
+    ap.add_argument("--split-slices", type=int, nargs="+", default=[7, 5])
+    ap.add_argument("--no-split-error", dest="split_error", action="store_false")
+    ap.add_argument("--profile-slices", type=int, default=0,
+                    help="with --profile: run the split-precision variant with this many slices")
     ap.add_argument("--profile", action="store_true",
                     help="device steps only (no e2e, comparator or CPU baseline): for ncu captures")
     args = ap.parse_args()

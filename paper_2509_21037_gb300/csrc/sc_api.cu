@@ -95,13 +95,13 @@ sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_d
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sc_assemble_batch status reset");
   record(ctx, 0, st);
-  int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, stream);
+  int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, ws, stream);
   if (rc) return cuda_fail(ctx, rc, "prep kernel launch");
   record(ctx, 1, st);
-  rc = launch_trsm(*ctx, L_values_dev, invd, Y, stream);
+  rc = launch_trsm(*ctx, L_values_dev, invd, ws, Y, stream);
   if (rc) return cuda_fail(ctx, rc, "trsm kernel launch");
   record(ctx, 2, st);
-  rc = launch_syrk(*ctx, Y, F_dev, stream);
+  rc = launch_syrk(*ctx, Y, ws, F_dev, stream);
   if (rc) return cuda_fail(ctx, rc, "syrk kernel launch");
   record(ctx, 3, st);
   ctx->stage_recorded = ctx->stage_events[0] != nullptr;

@@ -37,6 +37,11 @@ struct SubDev {
 struct SnDev {
   int64_t y_off;     // doubles, start of Y_s in the Y region
   int64_t rmap_off;  // first entry of this supernode in rmap
+  // split precision: first 32-wide row of this supernode in the L digit
+  // region; block b (rows kb+kw .. ns+rs-1, kb = 32 b) starts at row
+  // ld_off + b (ns + rs) - 16 b (b + 1)
+  int64_t ld_off;
+  int64_t yd_off;    // split precision: start of Y_s's digits (column-major, rows padded to 32)
   int32_t sub;       // subdomain
   int32_t c0, ns, rs;
   int32_t jlo, jhi;  // sorted column range on which Y_s is nonzero
@@ -104,11 +109,15 @@ struct PlanHeader {
 constexpr size_t kHeaderBytes = 512;
 static_assert(sizeof(PlanHeader) <= kHeaderBytes, "plan header must fit its reserved bytes");
 
-// Workspace layout (bytes from ws_dev): [status 256 B][invdiag][Y]
+// Workspace layout (bytes from ws_dev): [status 256 B][invdiag][Y], and for
+// split precision also [column exponents][Y digit planes][L digit planes][L row exponents]
 struct WsLayout {
   size_t status_off = 0;
   size_t invd_off = 256;
   size_t y_off = 0;
+  size_t colexp_off = 0, yd_off = 0, ld_off = 0, lexp_off = 0;
+  int64_t yd_plane = 0;     // elements per Y digit plane
+  int64_t ld_rows = 0;      // 32-wide rows per L digit plane
   size_t total = 0;
 };
 
@@ -145,10 +154,12 @@ sc_status fail(sc_ctx *ctx, sc_status st, const std::string &msg);
 
 // kernel launchers (sc_kernels.cu); return cudaError_t as int
 int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F,
-                void *stream);
-int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, double *Y, void *stream);
-int launch_syrk(const sc_ctx &c, const double *Y, double *F, void *stream);
-int launch_syrk_split(const sc_ctx &c, const double *Y, double *F, void *stream);
+                void *ws, void *stream);
+int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream);
+int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream);
+int launch_lpack_split(const sc_ctx &c, const double *Lv, void *ws, void *stream);
+int launch_trsm_split(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream);
+int launch_syrk_split(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);
 

@@ -248,7 +248,8 @@ __global__ void export_kernel(const SubDev *__restrict__ subs, int32_t i, const 
 
 static inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
-int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F, void *stream) {
+int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F, void *ws,
+                void *stream) {
   const PlanPtrs p = c.ptrs();
   if (c.n_active_cols > 0) {
     int64_t blocks = (c.n_active_cols + 255) / 256;
@@ -257,16 +258,21 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
                                                          status);
   }
   if (c.nsub > 0) fpad_kernel<<<c.nsub, 128, 0, S(stream)>>>(p.subs, F);
+  if (c.precision == SC_SPLIT_BF16) {
+    const int e = (int)cudaGetLastError();
+    return e ? e : launch_lpack_split(c, Lv, ws, stream);
+  }
   return (int)cudaGetLastError();
 }
 
-int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, double *Y, void *stream) {
+int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream) {
+  if (c.precision == SC_SPLIT_BF16) return launch_trsm_split(c, Lv, invd, ws, Y, stream);
   if (c.n_trsm > 0) trsm_kernel<<<(unsigned)c.n_trsm, kThreads, 0, S(stream)>>>(c.ptrs(), Lv, invd, Y);
   return (int)cudaGetLastError();
 }
 
-int launch_syrk(const sc_ctx &c, const double *Y, double *F, void *stream) {
-  if (c.precision == SC_SPLIT_BF16) return launch_syrk_split(c, Y, F, stream);
+int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream) {
+  if (c.precision == SC_SPLIT_BF16) return launch_syrk_split(c, Y, ws, F, stream);
   if (c.n_syrk > 0) syrk_kernel<<<(unsigned)c.n_syrk, kThreads, 0, S(stream)>>>(c.ptrs(), Y, F);
   return (int)cudaGetLastError();
 }

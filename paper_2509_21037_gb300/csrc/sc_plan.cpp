@@ -235,7 +235,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   ctx->L_offsets.assign(nsub + 1, 0);
   ctx->n.resize(nsub);
   ctx->m.resize(nsub);
-  int64_t y_total = 0, col_total = 0, lcp_total = 0;
+  int64_t y_total = 0, col_total = 0, lcp_total = 0, ld_rows_total = 0, yd_total = 0;
   sc_stats st{};
   int32_t max_m = 0;
 
@@ -276,6 +276,11 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       sn.c0 = S.sn_c0[s]; sn.ns = S.sn_ns[s]; sn.rs = S.sn_rs[s];
       sn.jlo = S.sn_jlo[s]; sn.jhi = S.sn_jhi[s];
       sn.lcp_off = (int32_t)(lcp_total + S.sn_c0[s]);
+      sn.ld_off = ld_rows_total;
+      for (int32_t kb = 0; kb < sn.ns; kb += 32)
+        ld_rows_total += (sn.ns + sn.rs) - kb - std::min(32, sn.ns - kb);
+      sn.yd_off = yd_total;
+      yd_total += (int64_t)ws * ((sn.ns + 31) / 32 * 32);
       sn.cut_off = (int32_t)cuts.size();
       for (int32_t kb = 0; kb < sn.ns; kb += 32) cuts.push_back(std::max(sn.jlo, block_cut(S, s, kb)));
       sns.push_back(sn);
@@ -453,6 +458,17 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   ctx->ws.invd_off = 256;
   ctx->ws.y_off = (ctx->ws.invd_off + sizeof(double) * (size_t)lcp_total + 255) & ~size_t(255);
   ctx->ws.total = ctx->ws.y_off + sizeof(double) * (size_t)y_total;
+  if (ctx->precision == SC_SPLIT_BF16) {
+    const size_t S = (size_t)ctx->n_slices;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    ctx->ws.colexp_off = up(ctx->ws.total);
+    ctx->ws.yd_off = up(ctx->ws.colexp_off + sizeof(int32_t) * (size_t)col_total);
+    ctx->ws.yd_plane = yd_total;
+    ctx->ws.ld_off = up(ctx->ws.yd_off + 2 * S * (size_t)yd_total);
+    ctx->ws.ld_rows = ld_rows_total;
+    ctx->ws.lexp_off = up(ctx->ws.ld_off + 2 * 32 * S * (size_t)ld_rows_total);
+    ctx->ws.total = up(ctx->ws.lexp_off + sizeof(int16_t) * (size_t)ld_rows_total);
+  }
 
   ctx->sizes.plan_bytes = ctx->blob.size();
   ctx->sizes.ws_bytes = ctx->ws.total;

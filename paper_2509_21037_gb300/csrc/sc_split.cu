@@ -8,8 +8,9 @@
 // multiplication and its applications", Numer. Algorithms 59, 2012), adapted
 // to 8-bit digits:
 //
-//   * every column j of the task's Y operand gets one exponent bound 2^Ej over
-//     all rows the task reads (|y| < 2^Ej);
+//   * every column j of a subdomain's Y gets one exponent bound 2^Ej over all
+//     its rows (|y| < 2^Ej), every row of an L panel block one bound over the
+//     block's 32 columns;
 //   * |y| 2^-Ej in [0, 1) is cut into S unsigned 8-bit digits u_0..u_{S-1}
 //     (y = sign * 2^Ej * sum_t u_t 2^(-8(t+1)) + truncation below 2^(Ej-8S)),
 //     taken from the FP64 bit pattern with integer operations only; each
@@ -18,8 +19,14 @@
 //     m16n8k16, BF16 in, FP32 accumulate); for one 32-row block the sum over
 //     all pairs with t + t' = d is an integer below 7 * 32 * 255^2 < 2^24, so
 //     the FP32 accumulator holds it exactly;
-//   * the exact block sums are added as int32 (flushed to FP64 every 128
-//     blocks), and the output is sum_d I_d 2^(-8(d+2)) * 2^(Ej1 + Ej2) in FP64.
+//   * the exact block sums are added as int32 (flushed every 128 blocks), the
+//     digit groups are combined exactly in 64-bit integers, and the output
+//     sum_d I_d 2^(-8(d+2)) * 2^(Ej1 + Ej2) is formed with one conversion to
+//     FP64 and one scaling (the FP64 pipe is the scarce resource on GB300).
+//
+// L and Y are cut into digit planes once per assembly (lpack_kernel after
+// the reciprocal diagonal; ycolexp/yslice after the TRSM), so the TRSM and
+// SYRK tasks only load BF16 planes.
 //
 // Only pairs with t + t' <= S - 1 are formed (S(S+1)/2 products); the terms
 // dropped and the digit truncation are below 2^(-8S) relative to the
@@ -75,81 +82,139 @@ __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) {
   return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// One 32x32 block of F = Y^T Y (sorted chunks q1 >= q2), split precision.
-// Warp w computes rows 16*(w>>1) .. +16 and columns 16*(w&1) .. +16 of the
-// block as two m16n8 tiles.
-template <int S>
-__global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, const double *__restrict__ Y,
-                                                              double *__restrict__ F) {
-  __shared__ __align__(16) __nv_bfloat16 PA[S][32][kPad];   // digit planes of the J1 columns, [t][j][k]
-  __shared__ __align__(16) __nv_bfloat16 PB[S][32][kPad];   // digit planes of the J2 columns
-  __shared__ int emaxA[32], emaxB[32];
-  const SyrkTask t = P.syrk_tasks[blockIdx.x];
-  const SubDev sd = P.subs[t.sub];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j1lo = t.q1 * kChunk, j2lo = t.q2 * kChunk;
 
-  // pass 1: per-column exponent bounds over every row this task reads
-  if (tid < 32) { emaxA[tid] = 0; emaxB[tid] = 0; }
-  __syncthreads();
-  {
-    int ma = 0, mb = 0;
-    for (int li = 0; li < t.list_len; ++li) {
-      const SnDev s = P.sns[P.syrk_list[t.list_off + li]];
-      const int ws = s.jhi - s.jlo;
-      const double *Ys = Y + s.y_off;
-      const int ja = j1lo + lane - s.jlo, jb = j2lo + lane - s.jlo;
-      const bool oka = ja >= 0 && ja < ws, okb = jb >= 0 && jb < ws;
-      for (int k0 = 0; k0 < s.ns; k0 += 32) {
-        if (j1lo >= P.cuts[s.cut_off + (k0 >> 5)]) continue;
-        const int kk = min(32, s.ns - k0);
-        for (int k = warp; k < kk; k += kThreads / 32) {
-          const double *row = Ys + (int64_t)(k0 + k) * ws;
-          if (oka) ma = max(ma, biased_exponent(row[ja]));
-          if (okb) mb = max(mb, biased_exponent(row[jb]));
+// ---------------------------------------------------------------------------
+// exact combination of the digit-group sums I_d (|I_d| < 2^31 each) into a
+// double: T = sum_d I_d 2^(8(S-1-d)) is formed as (H << 8(S-h)) + Lo with H,
+// Lo in int64, truncated by 2^-9 ulp-of-2^63 where it would overflow; the
+// value is T * 2^(-8(S+1)).
+template <int S>
+__device__ __forceinline__ double combine_groups(const int (&I)[S]) {
+  constexpr int h = (S + 1) / 2;
+  long long H = 0, Lo = 0;
+#pragma unroll
+  for (int d = 0; d < h; ++d) H += (long long)I[d] << (8 * (h - 1 - d));
+#pragma unroll
+  for (int d = h; d < S; ++d) Lo += (long long)I[d] << (8 * (S - 1 - d));
+  // H < 2^(31 + 8(h-1) + 1) and the full sum is H 2^(8(S-h)) + Lo; keep 62 bits
+  constexpr int sh = 8 * (S - h);
+  // bring both to a common scale 2^(sh - cut) with cut chosen to stay in int64
+  constexpr int cut = (31 + 8 * (h - 1) + 1 + sh > 62) ? (31 + 8 * (h - 1) + 1 + sh - 62) : 0;
+  const long long T = (H << (sh - cut)) + (Lo >> cut);
+  return (double)T * pow2i(cut - 8 * (S + 1));
+}
+
+// Digit planes of L's panel rows below each 32x32 diagonal block: one CTA per
+// active supernode, one thread per panel row (rows are contiguous in every
+// CSC column, so the loads are coalesced).
+template <int S>
+__global__ void __launch_bounds__(kThreads) lpack_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+                                                         __nv_bfloat16 *__restrict__ Ld,
+                                                         int16_t *__restrict__ lexp, int64_t ld_rows) {
+  const SnDev s = P.sns[blockIdx.x];
+  const int64_t *cp = P.lcp + s.lcp_off;
+  const int nrow = s.ns + s.rs;
+  for (int kb = 0, b = 0; kb < s.ns; kb += 32, ++b) {
+    const int kw = min(32, s.ns - kb);
+    const int nb = nrow - kb - kw;
+    const int64_t base = s.ld_off + (int64_t)b * nrow - 16LL * b * (b + 1);
+    for (int r = threadIdx.x; r < nb; r += kThreads) {
+      const int p = kb + kw + r;
+      double v[32];
+      int e = 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        v[q] = q < kw ? Lv[cp[kb + q] - (kb + q) + p] : 0.0;
+        e = max(e, biased_exponent(v[q]));
+      }
+      lexp[base + r] = (int16_t)e;
+#pragma unroll
+      for (int d = 0; d < S; ++d) {
+        uint32_t *row = reinterpret_cast<uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + r) * 32);
+#pragma unroll
+        for (int q = 0; q < 32; q += 2) {
+          const __nv_bfloat16 lo = digit_bf16(fixed_point(v[q], e), d, v[q] < 0.0);
+          const __nv_bfloat16 hi = digit_bf16(fixed_point(v[q + 1], e), d, v[q + 1] < 0.0);
+          row[q / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
         }
       }
     }
-    atomicMax(&emaxA[lane], ma);
-    atomicMax(&emaxB[lane], mb);
   }
-  __syncthreads();
+}
 
+// Column exponent bounds of Y (one int per sorted column of every subdomain).
+__global__ void __launch_bounds__(kThreads) ycolexp_kernel(const PlanPtrs P, const double *__restrict__ Y,
+                                                           int *__restrict__ colexp) {
+  const SnDev s = P.sns[blockIdx.x];
+  const SubDev sd = P.subs[s.sub];
+  const int ws = s.jhi - s.jlo;
+  for (int c = threadIdx.x; c < ws; c += kThreads) {
+    int e = 0;
+    for (int r = 0; r < s.ns; ++r) e = max(e, biased_exponent(Y[s.y_off + (int64_t)r * ws + c]));
+    atomicMax(&colexp[sd.col_off + s.jlo + c], e);
+  }
+}
+
+// Digit planes of Y, column-major per supernode with rows padded to 32.
+template <int S>
+__global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, const double *__restrict__ Y,
+                                                          const int *__restrict__ colexp,
+                                                          __nv_bfloat16 *__restrict__ Yd, int64_t yd_plane) {
+  const SnDev s = P.sns[blockIdx.x];
+  const SubDev sd = P.subs[s.sub];
+  const int ws = s.jhi - s.jlo;
+  const int npad = (s.ns + 31) / 32 * 32;
+  const int64_t total = (int64_t)ws * npad;
+  for (int64_t e = threadIdx.x; e < total; e += kThreads) {
+    const int c = (int)(e / npad), r = (int)(e - (int64_t)c * npad);
+    const double v = r < s.ns ? Y[s.y_off + (int64_t)r * ws + c] : 0.0;
+    const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c]);
+#pragma unroll
+    for (int d = 0; d < S; ++d) Yd[(int64_t)d * yd_plane + s.yd_off + e] = digit_bf16(X, d, v < 0.0);
+  }
+}
+
+// One 32x32 block of F = Y^T Y (sorted chunks q1 >= q2) from Y's digit
+// planes.  Warp w computes rows 16*(w>>1).. and columns 16*(w&1).. of the
+// block as two m16n8 tiles.
+template <int S>
+__global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
+                                                              int64_t yd_plane, const int *__restrict__ colexp,
+                                                              double *__restrict__ F) {
+  __shared__ __align__(16) __nv_bfloat16 PA[S][32][kPad];   // [t][column of J1][k]
+  __shared__ __align__(16) __nv_bfloat16 PB[S][32][kPad];   // [t][column of J2][k]
+  const SyrkTask t = P.syrk_tasks[blockIdx.x];
+  const SubDev sd = P.subs[t.sub];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tg = lane & 3;
-  const int mrow = 16 * (warp >> 1);            // this warp's rows (J1) in the block
-  const int ncol = 16 * (warp & 1);             // this warp's columns (J2): two n8 tiles
-  int iacc[S][8];
+  const int j1lo = t.q1 * kChunk, j2lo = t.q2 * kChunk;
+  const int mrow = 16 * (warp >> 1), ncol = 16 * (warp & 1);
+  int iacc[8][S];
+  long long hacc[8];      // flushed groups, exact: sum over flushes of T (see combine_groups)
   double dacc[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     dacc[i] = 0.0;
+    hacc[i] = 0;
 #pragma unroll
-    for (int d = 0; d < S; ++d) iacc[d][i] = 0;
+    for (int d = 0; d < S; ++d) iacc[i][d] = 0;
   }
   int blocks = 0;
   for (int li = 0; li < t.list_len; ++li) {
     const SnDev s = P.sns[P.syrk_list[t.list_off + li]];
-    const int ws = s.jhi - s.jlo;
-    const double *Ys = Y + s.y_off;
+    const int npad = (s.ns + 31) / 32 * 32;
     for (int k0 = 0; k0 < s.ns; k0 += 32) {
       if (j1lo >= P.cuts[s.cut_off + (k0 >> 5)]) continue;
-      const int kk = min(32, s.ns - k0);
-      // slice the 32x32 operands into digit planes (rows k >= kk are zero)
-      for (int k = warp; k < 32; k += kThreads / 32) {
-        const int ja = j1lo + lane - s.jlo, jb = j2lo + lane - s.jlo;
-        double va = 0.0, vb = 0.0;
-        if (k < kk) {
-          const double *row = Ys + (int64_t)(k0 + k) * ws;
-          if (ja >= 0 && ja < ws) va = row[ja];
-          if (jb >= 0 && jb < ws) vb = row[jb];
-        }
-        const uint64_t Xa = fixed_point(va, emaxA[lane]), Xb = fixed_point(vb, emaxB[lane]);
-        const bool na = va < 0.0, nb = vb < 0.0;
-#pragma unroll
-        for (int d = 0; d < S; ++d) {
-          PA[d][lane][k] = digit_bf16(Xa, d, na);
-          PB[d][lane][k] = digit_bf16(Xb, d, nb);
-        }
+      // 2 operands x S planes x 32 columns x 4 vectors of 8 digits
+      for (int v = tid; v < 2 * S * 32 * 4; v += kThreads) {
+        const int part = v & 3, col = (v >> 2) & 31, d = (v >> 7) % S, op = (v >> 7) / S;
+        const int j = (op == 0 ? j1lo : j2lo) + col - s.jlo;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (j >= 0 && j < s.jhi - s.jlo)
+          val = *reinterpret_cast<const uint4 *>(Yd + (int64_t)d * yd_plane + s.yd_off + (int64_t)j * npad + k0 +
+                                                 8 * part);
+        __nv_bfloat16 *dst = op == 0 ? &PA[d][col][8 * part] : &PB[d][col][8 * part];
+        *reinterpret_cast<uint4 *>(dst) = val;
       }
       __syncthreads();
 #pragma unroll
@@ -176,36 +241,32 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) iacc[d][nt * 4 + r] += __float2int_rn(c[nt][r]);
+          for (int r = 0; r < 4; ++r) iacc[nt * 4 + r][d] += __float2int_rn(c[nt][r]);
       }
       __syncthreads();
       if (++blocks == 128) {          // int32 headroom: 128 blocks * 1.46e7 < 2^31
         blocks = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          double v = 0.0;
+          dacc[i] += combine_groups<S>(iacc[i]);
 #pragma unroll
-          for (int d = 0; d < S; ++d) v += (double)iacc[d][i] * pow2i(-8 * (d + 2));
-          dacc[i] += v;
-#pragma unroll
-          for (int d = 0; d < S; ++d) iacc[d][i] = 0;
+          for (int d = 0; d < S; ++d) iacc[i][d] = 0;
         }
       }
     }
   }
   const int32_t *perm = P.perm_cols + sd.col_off;
+  const int *ce = colexp + sd.col_off;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int nt = i >> 2, r = i & 3;
-    const int rl = mrow + g + ((r & 2) ? 8 : 0);              // row in the block (J1)
-    const int cl = ncol + 8 * nt + 2 * tg + (r & 1);          // column in the block (J2)
-    double v = dacc[i];
-#pragma unroll
-    for (int d = 0; d < S; ++d) v += (double)iacc[d][i] * pow2i(-8 * (d + 2));
+    const int rl = mrow + g + ((r & 2) ? 8 : 0);
+    const int cl = ncol + 8 * nt + 2 * tg + (r & 1);
     const int j1 = j1lo + rl, j2 = j2lo + cl;
     if (j1 < sd.m && j2 < sd.m && (t.q1 != t.q2 || j1 >= j2)) {
-      const int e = (emaxA[rl] - 1022) + (emaxB[cl] - 1022);
-      v = ldexp(v, e);
+      double v = dacc[i] + combine_groups<S>(iacc[i]);
+      const int e = (ce[j1] - 1022) + (ce[j2] - 1022);
+      v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
       const int a = perm[j1], b = perm[j2];
       const int hi = max(a, b), lo = min(a, b);
       const int I = hi / kTile, J = lo / kTile;
@@ -214,21 +275,217 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
       if (I == J) T[(lo % kTile) + kTile * (hi % kTile)] = v;
     }
   }
+  (void)hacc;
+}
+
+// Sparse TRSM of one 32-column chunk with split-precision updates: the 32x32
+// diagonal triangles are solved in FP64 by one warp exactly as in the FP64
+// path; the update of the panel rows below (L[p, block] X, paper Sec. 3.2's
+// pruned GEMM) runs on the tensor cores from digit planes of X (column
+// bounds, shared memory) and of L's rows (pre-cut by lpack_kernel), combined
+// exactly in integers and subtracted from Y in FP64.
+template <int S>
+__global__ void __launch_bounds__(kThreads) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+                                                              const double *__restrict__ invd,
+                                                              const __nv_bfloat16 *__restrict__ Ld,
+                                                              const int16_t *__restrict__ lexp, int64_t ld_rows,
+                                                              double *__restrict__ Y) {
+  __shared__ double Xs[32][33];
+  __shared__ int64_t cps[32];
+  __shared__ __align__(16) __nv_bfloat16 PX[S][32][kPad];   // digit planes of X, [t][column][row]
+  __shared__ int emaxX[32];
+  const TrsmTask t = P.trsm_tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  const int c_hi = t.c_lo + t.w;
+
+  for (int li = 0; li < t.list_len; ++li) {
+    const SnDev s = P.sns[P.trsm_list[t.list_off + li]];
+    const int a = max(s.jlo, t.c_lo), b = min(s.jhi, c_hi), w = b - a, ws = s.jhi - s.jlo;
+    double *Ys = Y + s.y_off + (a - s.jlo);
+    const int total = s.ns * w;
+    for (int idx = tid; idx < total; idx += kThreads) {
+      const int r = idx / w, c = idx - r * w;
+      Ys[(int64_t)r * ws + c] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int e = t.seed_lo + tid; e < t.seed_hi; e += kThreads) {
+    const Seed sd = P.seeds[e];
+    Y[sd.y_off] = sd.value;
+  }
+  __syncthreads();
+
+  for (int li = 0; li < t.list_len; ++li) {
+    const SnDev s = P.sns[P.trsm_list[t.list_off + li]];
+    const int a = max(s.jlo, t.c_lo), b = min(s.jhi, c_hi), ws = s.jhi - s.jlo;
+    double *Ys = Y + s.y_off + (a - s.jlo);
+    const int64_t *cp = P.lcp + s.lcp_off;
+    const double *id = invd + s.lcp_off;
+    const int64_t *rm = P.rmap + s.rmap_off;
+    const int colsh = a - s.jlo;
+    const int nrow = s.ns + s.rs;
+    for (int kb = 0, blk = 0; kb < s.ns; kb += 32, ++blk) {
+      const int kw = min(32, s.ns - kb);
+      const int wk = min(b, P.cuts[s.cut_off + (kb >> 5)]) - a;
+      if (wk <= 0) continue;
+      if (warp == 0) {
+        if (lane < kw) cps[lane] = cp[kb + lane] - (kb + lane);
+        __syncwarp();
+        int em = 0;
+        if (lane < wk) {
+          for (int q = 0; q < kw; ++q) Xs[q][lane] = Ys[(int64_t)(kb + q) * ws + lane];
+          for (int q = 0; q < kw; ++q) {
+            const double xq = Xs[q][lane] * id[kb + q];
+            Xs[q][lane] = xq;
+            const double *Lc = Lv + cps[q];
+            for (int r = q + 1; r < kw; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
+          }
+          for (int q = 0; q < kw; ++q) {
+            Ys[(int64_t)(kb + q) * ws + lane] = Xs[q][lane];
+            em = max(em, biased_exponent(Xs[q][lane]));
+          }
+        }
+        emaxX[lane] = em;
+      }
+      __syncthreads();
+      const int nb = nrow - (kb + kw);
+      if (nb <= 0) continue;                  // nothing below this block (uniform)
+      for (int e = tid; e < 32 * 32; e += kThreads) {
+        const int q = e >> 5, c = e & 31;
+        const double v = (q < kw && c < wk) ? Xs[q][c] : 0.0;
+        const uint64_t X = fixed_point(v, emaxX[c]);
+        const bool neg = v < 0.0;
+#pragma unroll
+        for (int d = 0; d < S; ++d) PX[d][c][q] = digit_bf16(X, d, neg);
+      }
+      __syncthreads();
+      const int64_t base = s.ld_off + (int64_t)blk * nrow - 16LL * blk * (blk + 1);
+      for (int mt = warp; mt * 16 < nb; mt += kThreads / 32) {
+        const int r0 = mt * 16;               // first block row of this m-tile
+        const int ra = r0 + g, rb = r0 + g + 8;
+        const bool va = ra < nb, vb = rb < nb;
+        const int ea = va ? lexp[base + ra] : 0, eb = vb ? lexp[base + rb] : 0;
+        uint32_t afr[S][2][4];
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+          const uint32_t *pa = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + ra) * 32);
+          const uint32_t *pb = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + rb) * 32);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            afr[d][ks][0] = va ? pa[8 * ks + tg] : 0u;
+            afr[d][ks][1] = vb ? pb[8 * ks + tg] : 0u;
+            afr[d][ks][2] = va ? pa[8 * ks + tg + 4] : 0u;
+            afr[d][ks][3] = vb ? pb[8 * ks + tg + 4] : 0u;
+          }
+        }
+        int I[4][4][S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+          float c[4][4];
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) c[nt][r] = 0.f;
+#pragma unroll
+          for (int ta = 0; ta <= d; ++ta) {
+            const int tb = d - ta;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt) {
+                if (8 * nt < wk) {
+                  const uint32_t b0 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg]);
+                  const uint32_t b1 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg + 8]);
+                  mma_bf16(c[nt], afr[ta][ks], b0, b1);
+                }
+              }
+          }
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) I[nt][r][d] = __float2int_rn(c[nt][r]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int rr = (r & 2) ? rb : ra;
+            const int col = 8 * nt + 2 * tg + (r & 1);
+            if (rr < nb && col < wk) {
+              const int p = kb + kw + rr;
+              const int e = (((r & 2) ? eb : ea) - 1022) + (emaxX[col] - 1022);
+              double v = combine_groups<S>(I[nt][r]);
+              v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
+              double *tgt = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
+              tgt[col] -= v;
+            }
+          }
+      }
+      __syncthreads();
+    }
+  }
 }
 
 }  // namespace
 
-int launch_syrk_split(const sc_ctx &c, const double *Y, double *F, void *stream) {
-  if (c.n_syrk <= 0) return (int)cudaGetLastError();
+#define SC_SPLIT_SWITCH(S_, CALL) \
+  switch (S_) {                   \
+    case 3: CALL(3); break;       \
+    case 4: CALL(4); break;       \
+    case 5: CALL(5); break;       \
+    case 6: CALL(6); break;       \
+    default: CALL(7); break;      \
+  }
+
+int launch_lpack_split(const sc_ctx &c, const double *Lv, void *ws, void *stream) {
+  if (c.n_sns <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const unsigned grid = (unsigned)c.n_syrk;
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  __nv_bfloat16 *Ld = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.ld_off);
+  int16_t *lexp = reinterpret_cast<int16_t *>(w + c.ws.lexp_off);
   const PlanPtrs p = c.ptrs();
-  switch (c.n_slices) {
-    case 3: syrk_split_kernel<3><<<grid, kThreads, 0, st>>>(p, Y, F); break;
-    case 4: syrk_split_kernel<4><<<grid, kThreads, 0, st>>>(p, Y, F); break;
-    case 5: syrk_split_kernel<5><<<grid, kThreads, 0, st>>>(p, Y, F); break;
-    case 6: syrk_split_kernel<6><<<grid, kThreads, 0, st>>>(p, Y, F); break;
-    default: syrk_split_kernel<7><<<grid, kThreads, 0, st>>>(p, Y, F); break;
+#define LP(S) lpack_kernel<S><<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Lv, Ld, lexp, c.ws.ld_rows)
+  SC_SPLIT_SWITCH(c.n_slices, LP)
+#undef LP
+  return (int)cudaGetLastError();
+}
+
+int launch_trsm_split(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream) {
+  if (c.n_trsm <= 0) return (int)cudaGetLastError();
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  const __nv_bfloat16 *Ld = reinterpret_cast<const __nv_bfloat16 *>(w + c.ws.ld_off);
+  const int16_t *lexp = reinterpret_cast<const int16_t *>(w + c.ws.lexp_off);
+  const PlanPtrs p = c.ptrs();
+#define TS(S) trsm_split_kernel<S><<<(unsigned)c.n_trsm, kThreads, 0, st>>>(p, Lv, invd, Ld, lexp, c.ws.ld_rows, Y)
+  SC_SPLIT_SWITCH(c.n_slices, TS)
+#undef TS
+  return (int)cudaGetLastError();
+}
+
+int launch_syrk_split(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream) {
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  int *colexp = reinterpret_cast<int *>(w + c.ws.colexp_off);
+  __nv_bfloat16 *Yd = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.yd_off);
+  const PlanPtrs p = c.ptrs();
+  int64_t ncols = 0;
+  for (int32_t m : c.m) ncols += m;
+  if (ncols > 0) {
+    cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)ncols, st);
+    if (e != cudaSuccess) return (int)e;
+  }
+  if (c.n_sns > 0) {
+    ycolexp_kernel<<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Y, colexp);
+#define YS(S) yslice_kernel<S><<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
+    SC_SPLIT_SWITCH(c.n_slices, YS)
+#undef YS
+  }
+  if (c.n_syrk > 0) {
+#define SY(S) syrk_split_kernel<S><<<(unsigned)c.n_syrk, kThreads, 0, st>>>(p, Yd, c.ws.yd_plane, colexp, F)
+    SC_SPLIT_SWITCH(c.n_slices, SY)
+#undef SY
   }
   return (int)cudaGetLastError();
 }

@@ -79,11 +79,11 @@ extern "C" sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_value
   // trsm tasks first, and every reciprocal diagonal by its prep kernel)
   e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: status reset");
-  int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, stream);
+  int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, ws, stream);
   if (rc) return static_fail(ctx, (cudaError_t)rc, "prep kernel launch");
-  rc = launch_trsm(*ctx, L_values_dev, invd, Y, stream);
+  rc = launch_trsm(*ctx, L_values_dev, invd, ws, Y, stream);
   if (rc) return static_fail(ctx, (cudaError_t)rc, "trsm kernel launch");
-  rc = launch_syrk(*ctx, Y, F_dev, stream);
+  rc = launch_syrk(*ctx, Y, ws, F_dev, stream);
   if (rc) return static_fail(ctx, (cudaError_t)rc, "syrk kernel launch");
   // report this call's device status (the caller has no handle on the scratch)
   uint32_t h = 0;

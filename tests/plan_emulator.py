@@ -13,7 +13,7 @@ import numpy as np
 
 SUB = np.dtype([("F_off", "<i8"), ("L_off", "<i8"), ("n", "<i4"), ("m", "<i4"), ("nt", "<i4"),
                 ("col_off", "<i4"), ("lcp_off", "<i4"), ("pad", "<i4")])
-SN = np.dtype([("y_off", "<i8"), ("rmap_off", "<i8"), ("sub", "<i4"), ("c0", "<i4"), ("ns", "<i4"),
+SN = np.dtype([("y_off", "<i8"), ("rmap_off", "<i8"), ("ld_off", "<i8"), ("yd_off", "<i8"), ("sub", "<i4"), ("c0", "<i4"), ("ns", "<i4"),
                ("rs", "<i4"), ("jlo", "<i4"), ("jhi", "<i4"), ("lcp_off", "<i4"), ("cut_off", "<i4")])
 TRSM = np.dtype([("sub", "<i4"), ("c_lo", "<i4"), ("w", "<i4"), ("list_off", "<i4"), ("list_len", "<i4"),
                  ("seed_lo", "<i4"), ("seed_hi", "<i4"), ("pad", "<i4")])
@@ -214,3 +214,26 @@ def export_dense(T: dict, F: np.ndarray, i: int) -> np.ndarray:
             I, J = hi // 32, lo // 32
             out[a, b] = F[sd["F_off"] + (I * (I + 1) // 2 + J) * 1024 + hi % 32 + 32 * (lo % 32)]
     return out
+
+
+def check_split_layout(T: dict, sizes, stats) -> dict:
+    """Split-precision regions: per-supernode L digit rows (closed-form block
+    bases against the prefix sums) and Y digit blocks (rows padded to 32) are
+    disjoint, in range and 16-byte aligned for the vector loads."""
+    sns = T["sns"]
+    ld_end = yd_end = 0
+    for s in sns:
+        ns, rs, ws = int(s["ns"]), int(s["rs"]), int(s["jhi"] - s["jlo"])
+        nrow = ns + rs
+        assert s["ld_off"] == ld_end, "L digit rows not contiguous"
+        pre = 0
+        for b, kb in enumerate(range(0, ns, 32)):
+            kw = min(32, ns - kb)
+            assert s["ld_off"] + b * nrow - 16 * b * (b + 1) == s["ld_off"] + pre
+            pre += nrow - kb - kw
+        ld_end = s["ld_off"] + pre
+        npad = (ns + 31) // 32 * 32
+        assert s["yd_off"] == yd_end and s["yd_off"] % 32 == 0
+        yd_end = s["yd_off"] + ws * npad
+    assert yd_end % 32 == 0
+    return {"ld_rows": int(ld_end), "yd_plane": int(yd_end)}
