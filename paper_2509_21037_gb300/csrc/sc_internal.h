@@ -87,6 +87,7 @@ struct PlanPtrs {
   const ApplyTask *apply_tasks;
   const int32_t *active_cols; // global column indices whose reciprocal diagonal is needed
   const int32_t *cuts;       // per supernode and 32-row block: sorted columns >= cut are zero there
+  const int32_t *sblk;       // (active supernode, 32-row block) pairs, for the split-precision packing
 };
 
 struct Section {
@@ -96,14 +97,14 @@ struct Section {
 // First kHeaderBytes (512) bytes of the plan blob: a self-describing header, so that the
 // host copy (sc_export_plan) can be inspected or stored.  Sections follow in
 // the order of the arrays below, each 256-byte aligned.
-constexpr int kNumSections = 14;
+constexpr int kNumSections = 15;
 struct PlanHeader {
   uint32_t magic;      // 'SCPL'
   uint32_t version;    // 1
   int32_t nsub;
   int32_t chunk;       // kChunk
   int64_t n_sns, n_trsm, n_syrk, n_apply, n_cols, n_active_cols;
-  uint64_t sec_off[kNumSections];   // subs sns lcp rmap trsm trsm_list syrk syrk_list seeds perm lambda apply active cuts
+  uint64_t sec_off[kNumSections];   // subs sns lcp rmap trsm trsm_list syrk syrk_list seeds perm lambda apply active cuts sblk
   uint64_t sec_bytes[kNumSections];
 };
 constexpr size_t kHeaderBytes = 512;
@@ -131,8 +132,8 @@ struct sc_ctx {
   int64_t n_dual = 0;
   std::vector<uint8_t> blob;     // plan tables, 256-byte aligned sections
   sc::Section s_subs, s_sns, s_lcp, s_rmap, s_trsm, s_trsm_list, s_syrk, s_syrk_list, s_seeds,
-      s_perm, s_lambda, s_apply, s_active, s_cuts;
-  int64_t n_sns = 0, n_trsm = 0, n_syrk = 0, n_apply = 0, n_cols = 0, n_active_cols = 0;
+      s_perm, s_lambda, s_apply, s_active, s_cuts, s_sblk;
+  int64_t n_sns = 0, n_trsm = 0, n_syrk = 0, n_apply = 0, n_cols = 0, n_active_cols = 0, n_sblk = 0;
   std::vector<int64_t> F_offsets, L_offsets;
   std::vector<int32_t> n, m;
   sc::WsLayout ws;

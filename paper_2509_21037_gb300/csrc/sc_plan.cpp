@@ -229,6 +229,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<ApplyTask> apply;
   std::vector<int32_t> active_cols;
   std::vector<int32_t> cuts;
+  std::vector<int32_t> sblk;
   std::vector<double> trsm_cost, syrk_cost;
 
   ctx->F_offsets.assign(nsub + 1, 0);
@@ -282,7 +283,11 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       sn.yd_off = yd_total;
       yd_total += (int64_t)ws * ((sn.ns + 31) / 32 * 32);
       sn.cut_off = (int32_t)cuts.size();
-      for (int32_t kb = 0; kb < sn.ns; kb += 32) cuts.push_back(std::max(sn.jlo, block_cut(S, s, kb)));
+      for (int32_t kb = 0; kb < sn.ns; kb += 32) {
+        cuts.push_back(std::max(sn.jlo, block_cut(S, s, kb)));
+        sblk.push_back((int32_t)sns.size());
+        sblk.push_back(kb / 32);
+      }
       sns.push_back(sn);
       for (int32_t c = 0; c < sn.ns; ++c) active_cols.push_back(sn.lcp_off + c);
     }
@@ -431,6 +436,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   add_section(ctx->blob, ctx->s_apply, apply);
   add_section(ctx->blob, ctx->s_active, active_cols);
   add_section(ctx->blob, ctx->s_cuts, cuts);
+  add_section(ctx->blob, ctx->s_sblk, sblk);
   ctx->blob.resize((ctx->blob.size() + 255) & ~size_t(255));
   ctx->n_sns = (int64_t)sns.size();
   ctx->n_trsm = (int64_t)trsm.size();
@@ -438,6 +444,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   ctx->n_apply = (int64_t)apply.size();
   ctx->n_cols = lcp_total;
   ctx->n_active_cols = (int64_t)active_cols.size();
+  ctx->n_sblk = (int64_t)sblk.size() / 2;
   {
     PlanHeader h{};
     h.magic = 0x4C504353u;  // "SCPL"
@@ -449,7 +456,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     const Section *secs[kNumSections] = {&ctx->s_subs, &ctx->s_sns, &ctx->s_lcp, &ctx->s_rmap, &ctx->s_trsm,
                                          &ctx->s_trsm_list, &ctx->s_syrk, &ctx->s_syrk_list, &ctx->s_seeds,
                                          &ctx->s_perm, &ctx->s_lambda, &ctx->s_apply, &ctx->s_active,
-                                         &ctx->s_cuts};
+                                         &ctx->s_cuts, &ctx->s_sblk};
     for (int k = 0; k < kNumSections; ++k) { h.sec_off[k] = secs[k]->off; h.sec_bytes[k] = secs[k]->bytes; }
     std::memcpy(ctx->blob.data(), &h, sizeof(h));
   }
@@ -503,6 +510,7 @@ sc::PlanPtrs sc_ctx::ptrs() const {
   p.apply_tasks = reinterpret_cast<const ApplyTask *>(b + s_apply.off);
   p.active_cols = reinterpret_cast<const int32_t *>(b + s_active.off);
   p.cuts = reinterpret_cast<const int32_t *>(b + s_cuts.off);
+  p.sblk = reinterpret_cast<const int32_t *>(b + s_sblk.off);
   return p;
 }
 

@@ -84,93 +84,122 @@ __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) {
 
 
 // ---------------------------------------------------------------------------
-// exact combination of the digit-group sums I_d (|I_d| < 2^31 each) into a
-// double: T = sum_d I_d 2^(8(S-1-d)) is formed as (H << 8(S-h)) + Lo with H,
-// Lo in int64, truncated by 2^-9 ulp-of-2^63 where it would overflow; the
-// value is T * 2^(-8(S+1)).
+// Exact combination of the digit-group sums I_d into sum_d I_d 2^(-8(d+2)).
+// The groups are folded by Horner's rule into two int64 words,
+//   H = sum_{d<h} I_d 256^(h-1-d),   Lo = sum_{d>=h} I_d 256^(S-1-d),
+// so the value is H 2^(8(S-h)) + Lo, times 2^(-8(S+1)).
 template <int S>
-__device__ __forceinline__ double combine_groups(const int (&I)[S]) {
-  constexpr int h = (S + 1) / 2;
+struct Groups {
+  static constexpr int h = (S + 1) / 2;
   long long H = 0, Lo = 0;
-#pragma unroll
-  for (int d = 0; d < h; ++d) H += (long long)I[d] << (8 * (h - 1 - d));
-#pragma unroll
-  for (int d = h; d < S; ++d) Lo += (long long)I[d] << (8 * (S - 1 - d));
-  // H < 2^(31 + 8(h-1) + 1) and the full sum is H 2^(8(S-h)) + Lo; keep 62 bits
-  constexpr int sh = 8 * (S - h);
-  // bring both to a common scale 2^(sh - cut) with cut chosen to stay in int64
-  constexpr int cut = (31 + 8 * (h - 1) + 1 + sh > 62) ? (31 + 8 * (h - 1) + 1 + sh - 62) : 0;
-  const long long T = (H << (sh - cut)) + (Lo >> cut);
-  return (double)T * pow2i(cut - 8 * (S + 1));
-}
+  __device__ __forceinline__ void add(int d, int I) {       // Horner step, d ascending
+    if (d < h) H = H * 256 + I;
+    else Lo = Lo * 256 + I;
+  }
+  __device__ __forceinline__ void accumulate(int d, int I) {   // add I_d in place
+    if (d < h) H += (long long)I << (8 * (h - 1 - d));
+    else Lo += (long long)I << (8 * (S - 1 - d));
+  }
+  // |I_d| < 2^24 (one 32-row block): the sum needs 73 bits at most; drop the
+  // lowest cut = 11 bits of Lo (2^-53 of the column-bound product) and
+  // convert once.
+  __device__ __forceinline__ double value_block() const {
+    constexpr int sh = 8 * (S - h);
+    constexpr int bits = 24 + 8 * (S - 1) + 1;
+    constexpr int cut = bits > 62 ? bits - 62 : 0;
+    const long long T = (H << (sh - cut)) + (Lo >> cut);
+    return (double)T * pow2i(cut - 8 * (S + 1));
+  }
+  // |I_d| < 2^31 (many blocks): two conversions and one FMA
+  __device__ __forceinline__ double value_wide() const {
+    return fma((double)H, pow2i(8 * (S - h) - 8 * (S + 1)), (double)Lo * pow2i(-8 * (S + 1)));
+  }
+};
 
-// Digit planes of L's panel rows below each 32x32 diagonal block: one CTA per
-// active supernode, one thread per panel row (rows are contiguous in every
-// CSC column, so the loads are coalesced).
+// Digit planes of L's panel rows below one 32x32 diagonal block (one CTA per
+// (supernode, block) item; one thread per panel row, so every CSC column is
+// read contiguously).
 template <int S>
 __global__ void __launch_bounds__(kThreads) lpack_kernel(const PlanPtrs P, const double *__restrict__ Lv,
                                                          __nv_bfloat16 *__restrict__ Ld,
                                                          int16_t *__restrict__ lexp, int64_t ld_rows) {
-  const SnDev s = P.sns[blockIdx.x];
+  const int si = P.sblk[2 * blockIdx.x], b = P.sblk[2 * blockIdx.x + 1];
+  const SnDev s = P.sns[si];
   const int64_t *cp = P.lcp + s.lcp_off;
   const int nrow = s.ns + s.rs;
-  for (int kb = 0, b = 0; kb < s.ns; kb += 32, ++b) {
-    const int kw = min(32, s.ns - kb);
-    const int nb = nrow - kb - kw;
-    const int64_t base = s.ld_off + (int64_t)b * nrow - 16LL * b * (b + 1);
-    for (int r = threadIdx.x; r < nb; r += kThreads) {
-      const int p = kb + kw + r;
-      double v[32];
-      int e = 0;
+  const int kb = 32 * b, kw = min(32, s.ns - kb);
+  const int nb = nrow - kb - kw;
+  const int64_t base = s.ld_off + (int64_t)b * nrow - 16LL * b * (b + 1);
+  for (int r = threadIdx.x; r < nb; r += kThreads) {
+    const int p = kb + kw + r;
+    double v[32];
+    int e = 0;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        v[q] = q < kw ? Lv[cp[kb + q] - (kb + q) + p] : 0.0;
-        e = max(e, biased_exponent(v[q]));
-      }
-      lexp[base + r] = (int16_t)e;
+    for (int q = 0; q < 32; ++q) {
+      v[q] = q < kw ? Lv[cp[kb + q] - (kb + q) + p] : 0.0;
+      e = max(e, biased_exponent(v[q]));
+    }
+    lexp[base + r] = (int16_t)e;
 #pragma unroll
-      for (int d = 0; d < S; ++d) {
-        uint32_t *row = reinterpret_cast<uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + r) * 32);
+    for (int d = 0; d < S; ++d) {
+      uint32_t *row = reinterpret_cast<uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + r) * 32);
 #pragma unroll
-        for (int q = 0; q < 32; q += 2) {
-          const __nv_bfloat16 lo = digit_bf16(fixed_point(v[q], e), d, v[q] < 0.0);
-          const __nv_bfloat16 hi = digit_bf16(fixed_point(v[q + 1], e), d, v[q + 1] < 0.0);
-          row[q / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-        }
+      for (int q = 0; q < 32; q += 2) {
+        const __nv_bfloat16 lo = digit_bf16(fixed_point(v[q], e), d, v[q] < 0.0);
+        const __nv_bfloat16 hi = digit_bf16(fixed_point(v[q + 1], e), d, v[q + 1] < 0.0);
+        row[q / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
       }
     }
   }
 }
 
-// Column exponent bounds of Y (one int per sorted column of every subdomain).
+// Column exponent bounds of Y over one (supernode, 32-row block) item.
 __global__ void __launch_bounds__(kThreads) ycolexp_kernel(const PlanPtrs P, const double *__restrict__ Y,
                                                            int *__restrict__ colexp) {
-  const SnDev s = P.sns[blockIdx.x];
+  const int si = P.sblk[2 * blockIdx.x], b = P.sblk[2 * blockIdx.x + 1];
+  const SnDev s = P.sns[si];
   const SubDev sd = P.subs[s.sub];
   const int ws = s.jhi - s.jlo;
+  const int r0 = 32 * b, r1 = min(s.ns, r0 + 32);
   for (int c = threadIdx.x; c < ws; c += kThreads) {
     int e = 0;
-    for (int r = 0; r < s.ns; ++r) e = max(e, biased_exponent(Y[s.y_off + (int64_t)r * ws + c]));
-    atomicMax(&colexp[sd.col_off + s.jlo + c], e);
+    for (int r = r0; r < r1; ++r) e = max(e, biased_exponent(Y[s.y_off + (int64_t)r * ws + c]));
+    if (e) atomicMax(&colexp[sd.col_off + s.jlo + c], e);
   }
 }
 
-// Digit planes of Y, column-major per supernode with rows padded to 32.
+// Digit planes of Y for one (supernode, 32-row block) item: 32x32 tiles are
+// read row-wise (coalesced), transposed in shared memory and written
+// column-major (coalesced), rows padded to 32.
 template <int S>
 __global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, const double *__restrict__ Y,
                                                           const int *__restrict__ colexp,
                                                           __nv_bfloat16 *__restrict__ Yd, int64_t yd_plane) {
-  const SnDev s = P.sns[blockIdx.x];
+  __shared__ double Ts[32][33];
+  const int si = P.sblk[2 * blockIdx.x], b = P.sblk[2 * blockIdx.x + 1];
+  const SnDev s = P.sns[si];
   const SubDev sd = P.subs[s.sub];
   const int ws = s.jhi - s.jlo;
   const int npad = (s.ns + 31) / 32 * 32;
-  const int64_t total = (int64_t)ws * npad;
-  for (int64_t e = threadIdx.x; e < total; e += kThreads) {
-    const int c = (int)(e / npad), r = (int)(e - (int64_t)c * npad);
-    const double v = r < s.ns ? Y[s.y_off + (int64_t)r * ws + c] : 0.0;
-    const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c]);
+  const int r0 = 32 * b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < ws; c0 += 32) {
+    for (int i = warp; i < 32; i += kThreads / 32) {
+      const int r = r0 + i, c = c0 + lane;
+      Ts[i][lane] = (r < s.ns && c < ws) ? Y[s.y_off + (int64_t)r * ws + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = warp; j < 32; j += kThreads / 32) {
+      const int c = c0 + j;
+      if (c < ws) {
+        const double v = Ts[lane][j];
+        const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c]);
+        const int64_t e = s.yd_off + (int64_t)c * npad + r0 + lane;
 #pragma unroll
-    for (int d = 0; d < S; ++d) Yd[(int64_t)d * yd_plane + s.yd_off + e] = digit_bf16(X, d, v < 0.0);
+        for (int d = 0; d < S; ++d) Yd[(int64_t)d * yd_plane + e] = digit_bf16(X, d, v < 0.0);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -178,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, cons
 // planes.  Warp w computes rows 16*(w>>1).. and columns 16*(w&1).. of the
 // block as two m16n8 tiles.
 template <int S>
-__global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
+__global__ void __launch_bounds__(kThreads, 3) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
                                                               int64_t yd_plane, const int *__restrict__ colexp,
                                                               double *__restrict__ F) {
   __shared__ __align__(16) __nv_bfloat16 PA[S][32][kPad];   // [t][column of J1][k]
@@ -189,16 +218,12 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
   const int g = lane >> 2, tg = lane & 3;
   const int j1lo = t.q1 * kChunk, j2lo = t.q2 * kChunk;
   const int mrow = 16 * (warp >> 1), ncol = 16 * (warp & 1);
-  int iacc[8][S];
-  long long hacc[8];      // flushed groups, exact: sum over flushes of T (see combine_groups)
+  // per output: the Horner words of the digit-group sums, accumulated over
+  // blocks (linear, exact: < 128 blocks * 2^24 * 256^(h-1) < 2^63)
+  Groups<S> acc[8];
   double dacc[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    dacc[i] = 0.0;
-    hacc[i] = 0;
-#pragma unroll
-    for (int d = 0; d < S; ++d) iacc[i][d] = 0;
-  }
+  for (int i = 0; i < 8; ++i) dacc[i] = 0.0;
   int blocks = 0;
   for (int li = 0; li < t.list_len; ++li) {
     const SnDev s = P.sns[P.syrk_list[t.list_off + li]];
@@ -241,16 +266,15 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) iacc[nt * 4 + r][d] += __float2int_rn(c[nt][r]);
+          for (int r = 0; r < 4; ++r) acc[nt * 4 + r].accumulate(d, __float2int_rn(c[nt][r]));
       }
       __syncthreads();
-      if (++blocks == 128) {          // int32 headroom: 128 blocks * 1.46e7 < 2^31
+      if (++blocks == 128) {          // int64 headroom, see acc
         blocks = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          dacc[i] += combine_groups<S>(iacc[i]);
-#pragma unroll
-          for (int d = 0; d < S; ++d) iacc[i][d] = 0;
+          dacc[i] += acc[i].value_wide();
+          acc[i] = Groups<S>();
         }
       }
     }
@@ -264,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
     const int cl = ncol + 8 * nt + 2 * tg + (r & 1);
     const int j1 = j1lo + rl, j2 = j2lo + cl;
     if (j1 < sd.m && j2 < sd.m && (t.q1 != t.q2 || j1 >= j2)) {
-      double v = dacc[i] + combine_groups<S>(iacc[i]);
+      double v = dacc[i] + acc[i].value_wide();
       const int e = (ce[j1] - 1022) + (ce[j2] - 1022);
       v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
       const int a = perm[j1], b = perm[j2];
@@ -275,7 +299,6 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
       if (I == J) T[(lo % kTile) + kTile * (hi % kTile)] = v;
     }
   }
-  (void)hacc;
 }
 
 // Sparse TRSM of one 32-column chunk with split-precision updates: the 32x32
@@ -285,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) syrk_split_kernel(const PlanPtrs P, 
 // bounds, shared memory) and of L's rows (pre-cut by lpack_kernel), combined
 // exactly in integers and subtracted from Y in FP64.
 template <int S>
-__global__ void __launch_bounds__(kThreads) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+__global__ void __launch_bounds__(kThreads, 4) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
                                                               const double *__restrict__ invd,
                                                               const __nv_bfloat16 *__restrict__ Ld,
                                                               const int16_t *__restrict__ lexp, int64_t ld_rows,
@@ -379,35 +402,26 @@ __global__ void __launch_bounds__(kThreads) trsm_split_kernel(const PlanPtrs P, 
             afr[d][ks][3] = vb ? pb[8 * ks + tg + 4] : 0u;
           }
         }
-        int I[4][4][S];
 #pragma unroll
-        for (int d = 0; d < S; ++d) {
-          float c[4][4];
+        for (int nt = 0; nt < 4; ++nt) {
+          if (8 * nt >= wk) break;                   // uniform across the warp
+          Groups<S> gr[4];
 #pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
+          for (int d = 0; d < S; ++d) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int r = 0; r < 4; ++r) c[nt][r] = 0.f;
+            for (int ta = 0; ta <= d; ++ta) {
+              const int tb = d - ta;
 #pragma unroll
-          for (int ta = 0; ta <= d; ++ta) {
-            const int tb = d - ta;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-              for (int nt = 0; nt < 4; ++nt) {
-                if (8 * nt < wk) {
-                  const uint32_t b0 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg]);
-                  const uint32_t b1 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg + 8]);
-                  mma_bf16(c[nt], afr[ta][ks], b0, b1);
-                }
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t b0 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg]);
+                const uint32_t b1 = ld_pair(&PX[tb][8 * nt + g][16 * ks + 2 * tg + 8]);
+                mma_bf16(c, afr[ta][ks], b0, b1);
               }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) gr[r].add(d, __float2int_rn(c[r]));
           }
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) I[nt][r][d] = __float2int_rn(c[nt][r]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int rr = (r & 2) ? rb : ra;
@@ -415,12 +429,13 @@ __global__ void __launch_bounds__(kThreads) trsm_split_kernel(const PlanPtrs P, 
             if (rr < nb && col < wk) {
               const int p = kb + kw + rr;
               const int e = (((r & 2) ? eb : ea) - 1022) + (emaxX[col] - 1022);
-              double v = combine_groups<S>(I[nt][r]);
+              double v = gr[r].value_block();
               v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
               double *tgt = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
               tgt[col] -= v;
             }
           }
+        }
       }
       __syncthreads();
     }
@@ -439,13 +454,13 @@ __global__ void __launch_bounds__(kThreads) trsm_split_kernel(const PlanPtrs P, 
   }
 
 int launch_lpack_split(const sc_ctx &c, const double *Lv, void *ws, void *stream) {
-  if (c.n_sns <= 0) return (int)cudaGetLastError();
+  if (c.n_sblk <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
   __nv_bfloat16 *Ld = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.ld_off);
   int16_t *lexp = reinterpret_cast<int16_t *>(w + c.ws.lexp_off);
   const PlanPtrs p = c.ptrs();
-#define LP(S) lpack_kernel<S><<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Lv, Ld, lexp, c.ws.ld_rows)
+#define LP(S) lpack_kernel<S><<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Lv, Ld, lexp, c.ws.ld_rows)
   SC_SPLIT_SWITCH(c.n_slices, LP)
 #undef LP
   return (int)cudaGetLastError();
@@ -476,9 +491,9 @@ int launch_syrk_split(const sc_ctx &c, const double *Y, void *ws, double *F, voi
     cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)ncols, st);
     if (e != cudaSuccess) return (int)e;
   }
-  if (c.n_sns > 0) {
-    ycolexp_kernel<<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Y, colexp);
-#define YS(S) yslice_kernel<S><<<(unsigned)c.n_sns, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
+  if (c.n_sblk > 0) {
+    ycolexp_kernel<<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Y, colexp);
+#define YS(S) yslice_kernel<S><<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
     SC_SPLIT_SWITCH(c.n_slices, YS)
 #undef YS
   }

@@ -23,10 +23,11 @@ SEED = np.dtype([("y_off", "<i8"), ("value", "<f8")])
 APPLY = np.dtype([("sub", "<i4"), ("I", "<i4")])
 HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("nsub", "<i4"), ("chunk", "<i4"),
                    ("n_sns", "<i8"), ("n_trsm", "<i8"), ("n_syrk", "<i8"), ("n_apply", "<i8"),
-                   ("n_cols", "<i8"), ("n_active", "<i8"), ("sec_off", "<u8", 14), ("sec_bytes", "<u8", 14)])
+                   ("n_cols", "<i8"), ("n_active", "<i8"), ("sec_off", "<u8", 15), ("sec_bytes", "<u8", 15)])
 SECTIONS = [("subs", SUB), ("sns", SN), ("lcp", "<i8"), ("rmap", "<i8"), ("trsm", TRSM),
             ("trsm_list", "<i4"), ("syrk", SYRK), ("syrk_list", "<i4"), ("seeds", SEED),
-            ("perm", "<i4"), ("lambda", "<i4"), ("apply", APPLY), ("active", "<i4"), ("cuts", "<i4")]
+            ("perm", "<i4"), ("lambda", "<i4"), ("apply", APPLY), ("active", "<i4"), ("cuts", "<i4"),
+            ("sblk", "<i4")]
 
 
 def export_plan(plan) -> dict:
@@ -236,4 +237,7 @@ def check_split_layout(T: dict, sizes, stats) -> dict:
         assert s["yd_off"] == yd_end and s["yd_off"] % 32 == 0
         yd_end = s["yd_off"] + ws * npad
     assert yd_end % 32 == 0
+    sb = T["sblk"].reshape(-1, 2)
+    want = [(i, b) for i, s in enumerate(sns) for b in range((int(s["ns"]) + 31) // 32)]
+    assert [tuple(x) for x in sb.tolist()] == want
     return {"ld_rows": int(ld_end), "yd_plane": int(yd_end)}
