@@ -101,11 +101,16 @@ enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
  *            solves and the accumulation into Y and F stay FP64.  The error
  *            is below about 2^(-8 n_slices) relative to the product of the
  *            operands' column bounds; n_slices = 7 keeps 56 bits.
- * n_slices: 3..7 for SC_SPLIT_BF16 (0 selects 7); ignored for SC_FP64. */
+ * n_slices: 3..7 for SC_SPLIT_BF16 (0 selects 7); ignored for SC_FP64.
+ * sub_slices: optional per-subdomain variant, nsub entries (host, read during
+ *            sc_plan): 0 = FP64, 3..7 = split precision with that many
+ *            digits; when given it overrides precision/n_slices.  Subdomains
+ *            of each variant run as their own launch group. */
 typedef struct {
   int32_t precision;
   int32_t n_slices;
-  int32_t reserved[6]; /* must be zero */
+  const int8_t *sub_slices;
+  int32_t reserved[4]; /* must be zero */
 } sc_options;
 
 typedef struct {

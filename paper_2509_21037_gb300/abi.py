@@ -24,7 +24,7 @@ SC_FP64, SC_SPLIT_BF16 = 0, 1
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("reserved", c_i32 * 6)]
+    _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("sub_slices", c_vp), ("reserved", c_i32 * 4)]
 
 
 class Sizes(ctypes.Structure):

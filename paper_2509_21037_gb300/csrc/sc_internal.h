@@ -126,8 +126,11 @@ struct WsLayout {
 
 struct sc_ctx {
   std::string err;
-  int32_t precision = SC_FP64;
-  int32_t n_slices = 0;
+  int32_t precision = SC_FP64;       // SC_SPLIT_BF16 when any subdomain runs split
+  int32_t n_slices = 0;              // largest digit count of any subdomain (plane sizing)
+  std::vector<int8_t> sub_var;       // per subdomain: 0 = FP64, 3..7 = split digits
+  // launch groups by variant (index 0 = FP64, 3..7 = digits): first item, count
+  int64_t trsm_grp[8][2] = {}, syrk_grp[8][2] = {}, sblk_grp[8][2] = {};
   int32_t nsub = 0;
   int64_t n_dual = 0;
   std::vector<uint8_t> blob;     // plan tables, 256-byte aligned sections
@@ -158,9 +161,12 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
                 void *ws, void *stream);
 int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream);
 int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream);
-int launch_lpack_split(const sc_ctx &c, const double *Lv, void *ws, void *stream);
-int launch_trsm_split(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream);
-int launch_syrk_split(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream);
+// split-precision launchers: one variant group (S digits, items [base, base + count))
+int launch_lpack_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, void *ws, void *stream);
+int launch_trsm_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, const double *invd,
+                      void *ws, double *Y, void *stream);
+int launch_yslice_split(const sc_ctx &c, const double *Y, void *ws, void *stream);   // all split groups
+int launch_syrk_split(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);
 

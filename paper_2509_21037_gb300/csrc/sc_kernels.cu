@@ -258,23 +258,36 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
                                                          status);
   }
   if (c.nsub > 0) fpad_kernel<<<c.nsub, 128, 0, S(stream)>>>(p.subs, F);
-  if (c.precision == SC_SPLIT_BF16) {
-    const int e = (int)cudaGetLastError();
-    return e ? e : launch_lpack_split(c, Lv, ws, stream);
-  }
-  return (int)cudaGetLastError();
+  int e = (int)cudaGetLastError();
+  for (int v = 3; v < 8 && !e; ++v)
+    if (c.sblk_grp[v][1] > 0) e = launch_lpack_split(c, v, c.sblk_grp[v][0], c.sblk_grp[v][1], Lv, ws, stream);
+  return e;
 }
 
 int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream) {
-  if (c.precision == SC_SPLIT_BF16) return launch_trsm_split(c, Lv, invd, ws, Y, stream);
-  if (c.n_trsm > 0) trsm_kernel<<<(unsigned)c.n_trsm, kThreads, 0, S(stream)>>>(c.ptrs(), Lv, invd, Y);
-  return (int)cudaGetLastError();
+  if (c.trsm_grp[0][1] > 0) {
+    PlanPtrs p = c.ptrs();
+    p.trsm_tasks += c.trsm_grp[0][0];
+    trsm_kernel<<<(unsigned)c.trsm_grp[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
+  }
+  int e = (int)cudaGetLastError();
+  for (int v = 3; v < 8 && !e; ++v)
+    if (c.trsm_grp[v][1] > 0) e = launch_trsm_split(c, v, c.trsm_grp[v][0], c.trsm_grp[v][1], Lv, invd, ws, Y, stream);
+  return e;
 }
 
 int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream) {
-  if (c.precision == SC_SPLIT_BF16) return launch_syrk_split(c, Y, ws, F, stream);
-  if (c.n_syrk > 0) syrk_kernel<<<(unsigned)c.n_syrk, kThreads, 0, S(stream)>>>(c.ptrs(), Y, F);
-  return (int)cudaGetLastError();
+  int e = 0;
+  if (c.n_slices > 0) e = launch_yslice_split(c, Y, ws, stream);
+  if (!e && c.syrk_grp[0][1] > 0) {
+    PlanPtrs p = c.ptrs();
+    p.syrk_tasks += c.syrk_grp[0][0];
+    syrk_kernel<<<(unsigned)c.syrk_grp[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
+    e = (int)cudaGetLastError();
+  }
+  for (int v = 3; v < 8 && !e; ++v)
+    if (c.syrk_grp[v][1] > 0) e = launch_syrk_split(c, v, c.syrk_grp[v][0], c.syrk_grp[v][1], ws, F, stream);
+  return e;
 }
 
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream) {

@@ -229,8 +229,9 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<ApplyTask> apply;
   std::vector<int32_t> active_cols;
   std::vector<int32_t> cuts;
-  std::vector<int32_t> sblk;
+  std::vector<int32_t> sblk_v[8];
   std::vector<double> trsm_cost, syrk_cost;
+  std::vector<int8_t> trsm_var, syrk_var;
 
   ctx->F_offsets.assign(nsub + 1, 0);
   ctx->L_offsets.assign(nsub + 1, 0);
@@ -277,16 +278,21 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       sn.c0 = S.sn_c0[s]; sn.ns = S.sn_ns[s]; sn.rs = S.sn_rs[s];
       sn.jlo = S.sn_jlo[s]; sn.jhi = S.sn_jhi[s];
       sn.lcp_off = (int32_t)(lcp_total + S.sn_c0[s]);
-      sn.ld_off = ld_rows_total;
-      for (int32_t kb = 0; kb < sn.ns; kb += 32)
-        ld_rows_total += (sn.ns + sn.rs) - kb - std::min(32, sn.ns - kb);
-      sn.yd_off = yd_total;
-      yd_total += (int64_t)ws * ((sn.ns + 31) / 32 * 32);
+      const int var = ctx->sub_var[i];
+      if (var) {
+        sn.ld_off = ld_rows_total;
+        for (int32_t kb = 0; kb < sn.ns; kb += 32)
+          ld_rows_total += (sn.ns + sn.rs) - kb - std::min(32, sn.ns - kb);
+        sn.yd_off = yd_total;
+        yd_total += (int64_t)ws * ((sn.ns + 31) / 32 * 32);
+      }
       sn.cut_off = (int32_t)cuts.size();
       for (int32_t kb = 0; kb < sn.ns; kb += 32) {
         cuts.push_back(std::max(sn.jlo, block_cut(S, s, kb)));
-        sblk.push_back((int32_t)sns.size());
-        sblk.push_back(kb / 32);
+        if (var) {
+          sblk_v[var].push_back((int32_t)sns.size());
+          sblk_v[var].push_back(kb / 32);
+        }
       }
       sns.push_back(sn);
       for (int32_t c = 0; c < sn.ns; ++c) active_cols.push_back(sn.lcp_off + c);
@@ -359,6 +365,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       st.flops_trsm_exec += exec;
       trsm.push_back(t);
       trsm_cost.push_back(exec + 1e3 * t.list_len);
+      trsm_var.push_back(ctx->sub_var[i]);
     }
     // chunk-pair lists (lower triangle of sorted chunks)
     for (int32_t q1 = 0; q1 < nchunk; ++q1) {
@@ -384,6 +391,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
         st.flops_syrk_exec += exec;
         syrk.push_back(t);
         syrk_cost.push_back(exec + 1e3 * (t.list_len + 1));
+        syrk_var.push_back(ctx->sub_var[i]);
       }
     }
     for (int32_t s = 0; s < nsn; ++s) {
@@ -402,24 +410,43 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     col_total += m;
     lcp_total += n;
   }
-  // largest tasks first: the block scheduler hands out CTAs roughly in index order
-  auto order_by = [](const std::vector<double> &cost) {
+  // grouped by variant (one launch per group), largest tasks first inside a
+  // group: the block scheduler hands out CTAs roughly in index order
+  auto order_by = [](const std::vector<double> &cost, const std::vector<int8_t> &var) {
     std::vector<int32_t> o(cost.size());
     std::iota(o.begin(), o.end(), 0);
-    std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) {
+      return var[a] != var[b] ? var[a] < var[b] : cost[a] > cost[b];
+    });
     return o;
   };
+  auto groups = [](const std::vector<int8_t> &var, const std::vector<int32_t> &o, int64_t (&grp)[8][2]) {
+    for (auto &g : grp) g[0] = g[1] = 0;
+    for (size_t k = 0; k < o.size(); ++k) {
+      const int v = var[o[k]];
+      if (grp[v][1] == 0) grp[v][0] = (int64_t)k;
+      grp[v][1]++;
+    }
+  };
   {
-    auto o = order_by(trsm_cost);
+    auto o = order_by(trsm_cost, trsm_var);
+    groups(trsm_var, o, ctx->trsm_grp);
     std::vector<TrsmTask> t2(trsm.size());
     for (size_t k = 0; k < o.size(); ++k) t2[k] = trsm[o[k]];
     trsm.swap(t2);
   }
   {
-    auto o = order_by(syrk_cost);
+    auto o = order_by(syrk_cost, syrk_var);
+    groups(syrk_var, o, ctx->syrk_grp);
     std::vector<SyrkTask> t2(syrk.size());
     for (size_t k = 0; k < o.size(); ++k) t2[k] = syrk[o[k]];
     syrk.swap(t2);
+  }
+  std::vector<int32_t> sblk;
+  for (int v = 0; v < 8; ++v) {
+    ctx->sblk_grp[v][0] = (int64_t)sblk.size() / 2;
+    ctx->sblk_grp[v][1] = (int64_t)sblk_v[v].size() / 2;
+    sblk.insert(sblk.end(), sblk_v[v].begin(), sblk_v[v].end());
   }
   ctx->blob.assign(kHeaderBytes, 0);
   add_section(ctx->blob, ctx->s_subs, subs);
@@ -465,7 +492,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   ctx->ws.invd_off = 256;
   ctx->ws.y_off = (ctx->ws.invd_off + sizeof(double) * (size_t)lcp_total + 255) & ~size_t(255);
   ctx->ws.total = ctx->ws.y_off + sizeof(double) * (size_t)y_total;
-  if (ctx->precision == SC_SPLIT_BF16) {
+  if (ctx->n_slices > 0) {
     const size_t S = (size_t)ctx->n_slices;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     ctx->ws.colexp_off = up(ctx->ws.total);
@@ -531,10 +558,20 @@ sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomain
              (opt->n_slices < 3 || opt->n_slices > 7)) {
     st = fail(ctx, SC_ERR_INVALID_ARG, "n_slices must be 3..7 (or 0 for 7)");
   } else {
-    if (opt) {
-      ctx->precision = opt->precision;
-      ctx->n_slices = opt->precision == SC_SPLIT_BF16 ? (opt->n_slices ? opt->n_slices : 7) : 0;
+    const int8_t dflt = (opt && opt->precision == SC_SPLIT_BF16) ? (int8_t)(opt->n_slices ? opt->n_slices : 7) : 0;
+    ctx->sub_var.assign(nsub > 0 ? nsub : 0, dflt);
+    for (int32_t i = 0; i < nsub && opt && opt->sub_slices; ++i) {
+      const int8_t v = opt->sub_slices[i];
+      if (v != 0 && (v < 3 || v > 7)) {
+        st = fail(ctx, SC_ERR_INVALID_ARG, "sub_slices entries must be 0 or 3..7");
+        break;
+      }
+      ctx->sub_var[i] = v;
     }
+    for (int8_t v : ctx->sub_var) ctx->n_slices = std::max<int32_t>(ctx->n_slices, v);
+    ctx->precision = ctx->n_slices > 0 ? SC_SPLIT_BF16 : SC_FP64;
+  }
+  if (st == SC_OK && !(nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0)) {
     ctx->nsub = nsub;
     ctx->n_dual = n_dual;
     try {

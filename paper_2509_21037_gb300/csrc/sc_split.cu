@@ -453,55 +453,77 @@ __global__ void __launch_bounds__(kThreads, 4) trsm_split_kernel(const PlanPtrs 
     default: CALL(7); break;      \
   }
 
-int launch_lpack_split(const sc_ctx &c, const double *Lv, void *ws, void *stream) {
-  if (c.n_sblk <= 0) return (int)cudaGetLastError();
+int launch_lpack_split(const sc_ctx &c, int S_, int64_t base, int64_t count, const double *Lv, void *ws,
+                       void *stream) {
+  if (count <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
   __nv_bfloat16 *Ld = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.ld_off);
   int16_t *lexp = reinterpret_cast<int16_t *>(w + c.ws.lexp_off);
-  const PlanPtrs p = c.ptrs();
-#define LP(S) lpack_kernel<S><<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Lv, Ld, lexp, c.ws.ld_rows)
-  SC_SPLIT_SWITCH(c.n_slices, LP)
+  PlanPtrs p = c.ptrs();
+  p.sblk += 2 * base;
+#define LP(S) lpack_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Lv, Ld, lexp, c.ws.ld_rows)
+  SC_SPLIT_SWITCH(S_, LP)
 #undef LP
   return (int)cudaGetLastError();
 }
 
-int launch_trsm_split(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream) {
-  if (c.n_trsm <= 0) return (int)cudaGetLastError();
+int launch_trsm_split(const sc_ctx &c, int S_, int64_t base, int64_t count, const double *Lv, const double *invd,
+                      void *ws, double *Y, void *stream) {
+  if (count <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
   const __nv_bfloat16 *Ld = reinterpret_cast<const __nv_bfloat16 *>(w + c.ws.ld_off);
   const int16_t *lexp = reinterpret_cast<const int16_t *>(w + c.ws.lexp_off);
-  const PlanPtrs p = c.ptrs();
-#define TS(S) trsm_split_kernel<S><<<(unsigned)c.n_trsm, kThreads, 0, st>>>(p, Lv, invd, Ld, lexp, c.ws.ld_rows, Y)
-  SC_SPLIT_SWITCH(c.n_slices, TS)
+  PlanPtrs p = c.ptrs();
+  p.trsm_tasks += base;
+#define TS(S) trsm_split_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Lv, invd, Ld, lexp, c.ws.ld_rows, Y)
+  SC_SPLIT_SWITCH(S_, TS)
 #undef TS
   return (int)cudaGetLastError();
 }
 
-int launch_syrk_split(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream) {
+int launch_yslice_split(const sc_ctx &c, const double *Y, void *ws, void *stream) {
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
   int *colexp = reinterpret_cast<int *>(w + c.ws.colexp_off);
   __nv_bfloat16 *Yd = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.yd_off);
-  const PlanPtrs p = c.ptrs();
   int64_t ncols = 0;
   for (int32_t m : c.m) ncols += m;
   if (ncols > 0) {
     cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)ncols, st);
     if (e != cudaSuccess) return (int)e;
   }
-  if (c.n_sblk > 0) {
-    ycolexp_kernel<<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Y, colexp);
-#define YS(S) yslice_kernel<S><<<(unsigned)c.n_sblk, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
-    SC_SPLIT_SWITCH(c.n_slices, YS)
+  for (int v = 3; v < 8; ++v) {
+    const int64_t base = c.sblk_grp[v][0], count = c.sblk_grp[v][1];
+    if (count <= 0) continue;
+    PlanPtrs p = c.ptrs();
+    p.sblk += 2 * base;
+    ycolexp_kernel<<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp);
+  }
+  for (int v = 3; v < 8; ++v) {
+    const int64_t base = c.sblk_grp[v][0], count = c.sblk_grp[v][1];
+    if (count <= 0) continue;
+    PlanPtrs p = c.ptrs();
+    p.sblk += 2 * base;
+#define YS(S) yslice_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
+    SC_SPLIT_SWITCH(v, YS)
 #undef YS
   }
-  if (c.n_syrk > 0) {
-#define SY(S) syrk_split_kernel<S><<<(unsigned)c.n_syrk, kThreads, 0, st>>>(p, Yd, c.ws.yd_plane, colexp, F)
-    SC_SPLIT_SWITCH(c.n_slices, SY)
+  return (int)cudaGetLastError();
+}
+
+int launch_syrk_split(const sc_ctx &c, int S_, int64_t base, int64_t count, void *ws, double *F, void *stream) {
+  if (count <= 0) return (int)cudaGetLastError();
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  const int *colexp = reinterpret_cast<const int *>(w + c.ws.colexp_off);
+  const __nv_bfloat16 *Yd = reinterpret_cast<const __nv_bfloat16 *>(w + c.ws.yd_off);
+  PlanPtrs p = c.ptrs();
+  p.syrk_tasks += base;
+#define SY(S) syrk_split_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Yd, c.ws.yd_plane, colexp, F)
+  SC_SPLIT_SWITCH(S_, SY)
 #undef SY
-  }
   return (int)cudaGetLastError();
 }
 

@@ -34,7 +34,8 @@ class Plan:
     (L pattern, B^T in L's ordering, lambda map).
     """
 
-    def __init__(self, subdomains: Sequence, n_dual: int, precision: int = abi.SC_FP64, n_slices: int = 0):
+    def __init__(self, subdomains: Sequence, n_dual: int, precision: int = abi.SC_FP64, n_slices: int = 0,
+                 sub_slices: Optional[Sequence[int]] = None):
         self.lib = _native.sc_lib()
         self.nsub = len(subdomains)
         self.n_dual = int(n_dual)
@@ -53,6 +54,10 @@ class Plan:
         opt = abi.Options()
         opt.precision = precision
         opt.n_slices = n_slices
+        if sub_slices is not None:
+            self._sub_slices = np.ascontiguousarray(np.asarray(sub_slices), dtype=np.int8)
+            assert len(self._sub_slices) == self.nsub
+            opt.sub_slices = self._sub_slices.ctypes.data
         st = self.lib.sc_plan(ctypes.byref(h), self.nsub, descs, self.n_dual, ctypes.byref(opt))
         self.h = h
         if st != abi.SC_OK:

@@ -217,13 +217,20 @@ def export_dense(T: dict, F: np.ndarray, i: int) -> np.ndarray:
     return out
 
 
-def check_split_layout(T: dict, sizes, stats) -> dict:
+def check_split_layout(T: dict, sizes, stats, sub_var=None) -> dict:
     """Split-precision regions: per-supernode L digit rows (closed-form block
-    bases against the prefix sums) and Y digit blocks (rows padded to 32) are
-    disjoint, in range and 16-byte aligned for the vector loads."""
+    bases against the prefix sums) and Y digit blocks (rows padded to 32) of
+    the split subdomains are disjoint, in range and 16-byte aligned for the
+    vector loads; the (supernode, block) work list is grouped by variant."""
     sns = T["sns"]
+    nsub = len(T["subs"])
+    sub_var = [1] * nsub if sub_var is None else list(sub_var)
     ld_end = yd_end = 0
-    for s in sns:
+    want = {}
+    for i, s in enumerate(sns):
+        v = sub_var[int(s["sub"])]
+        if not v:
+            continue
         ns, rs, ws = int(s["ns"]), int(s["rs"]), int(s["jhi"] - s["jlo"])
         nrow = ns + rs
         assert s["ld_off"] == ld_end, "L digit rows not contiguous"
@@ -232,12 +239,12 @@ def check_split_layout(T: dict, sizes, stats) -> dict:
             kw = min(32, ns - kb)
             assert s["ld_off"] + b * nrow - 16 * b * (b + 1) == s["ld_off"] + pre
             pre += nrow - kb - kw
+            want.setdefault(v, []).append((i, b))
         ld_end = s["ld_off"] + pre
         npad = (ns + 31) // 32 * 32
         assert s["yd_off"] == yd_end and s["yd_off"] % 32 == 0
         yd_end = s["yd_off"] + ws * npad
     assert yd_end % 32 == 0
-    sb = T["sblk"].reshape(-1, 2)
-    want = [(i, b) for i, s in enumerate(sns) for b in range((int(s["ns"]) + 31) // 32)]
-    assert [tuple(x) for x in sb.tolist()] == want
+    sb = [tuple(x) for x in T["sblk"].reshape(-1, 2).tolist()]
+    assert sb == [x for v in sorted(want) for x in want[v]]
     return {"ld_rows": int(ld_end), "yd_plane": int(yd_end)}

@@ -219,3 +219,9 @@ def test_host_implicit_apply_matches_oracle(threads):
     qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains), [s.lambda_map for s in prob.subdomains],
                            lam, prob.n_dual)
     assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+
+
+def test_mlp_header_symbols_exported():
+    names = _declared("sc_mlp.h")
+    lib = _native.sc_lib()
+    assert names and all(hasattr(lib, n) for n in names)

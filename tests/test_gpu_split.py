@@ -50,3 +50,24 @@ def test_split_error_by_slices(dev, name):
     for s in (3, 4, 5, 6):
         assert err[s] <= 2.0 ** (-8 * s) * 1e3          # ~2^-8S times a modest growth factor
         assert err[s] >= err[s + 1] or err[s + 1] <= 2 * err[0]
+
+
+def test_mixed_variants_in_one_batch(dev):
+    """Per-subdomain kernel variants (0 = FP64, 3..7 digits) in one plan: each
+    subdomain's F carries its own variant's accuracy."""
+    prob = synth.cube_heat_3d(parts=2, k=6, coef_seed=8)
+    fs = host.factorize_problem(prob.subdomains)
+    Fo = oracle.dual_operators(prob.subdomains, refine=1)
+    var = [0, 7, 5, 4, 0, 6, 3, 7]
+    plan = sc.Plan(fs, prob.n_dual, sub_slices=var).upload(dev)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    F = plan.new_F(dev)
+    F.fill_(float("nan"))
+    plan.assemble(Lv, F)
+    assert plan.device_status() == abi.SC_OK
+    for i, v in enumerate(var):
+        err = oracle.relative_frobenius(plan.export(F, i).cpu().numpy(), Fo[i])
+        bound = 1e-12 if v in (0, 7) else 2.0 ** (-8 * v) * 1e3
+        assert err <= bound, (i, v, err)
+        if v in (3, 4, 5):
+            assert err > 1e-13                       # really ran in reduced precision
