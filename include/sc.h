@@ -105,7 +105,11 @@ enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
  * sub_slices: optional per-subdomain variant, nsub entries (host, read during
  *            sc_plan): 0 = FP64, 3..7 = split precision with that many
  *            digits; when given it overrides precision/n_slices.  Subdomains
- *            of each variant run as their own launch group. */
+ *            of each variant run as their own launch group; when a batch has
+ *            several, sc_assemble_batch runs the groups concurrently on
+ *            library-owned streams forked from and joined back into the
+ *            caller's stream with events (the call stays asynchronous and
+ *            ordered on the caller's stream). */
 typedef struct {
   int32_t precision;
   int32_t n_slices;
@@ -134,6 +138,7 @@ typedef struct {
   int64_t n_supernodes;     /* active supernodes (touched by some column) */
   int64_t n_trsm_tasks, n_syrk_tasks, n_apply_tasks;
   int64_t y_doubles;        /* workspace doubles of the sparse Y */
+  int64_t max_supernode;    /* columns of the largest active supernode */
 } sc_stats;
 
 /* ---- initialization -------------------------------------------------------- */
@@ -221,7 +226,9 @@ sc_status sc_export_F(sc_ctx *ctx, const double *F_dev, int32_t i, double *dst_d
 
 /* Stage timing.  With timing on, sc_assemble_batch records a CUDA event on its
  * stream before the first kernel and after each stage: [0] prep (reciprocal
- * diagonal, F padding), [1] sparse TRSM, [2] pruned SYRK.  sc_stage_times
+ * diagonal, F padding), [1] sparse TRSM, [2] pruned SYRK (for a batch with
+ * several variant groups, [1] covers the TRSM and the SYRK of all groups and
+ * [2] is zero).  sc_stage_times
  * synchronises on the last recorded event and writes up to n elapsed times
  * (milliseconds) of the last timed call.  Events are created by
  * sc_enable_stage_timing(ctx, 1) on the current device and destroyed by

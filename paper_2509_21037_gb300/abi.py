@@ -37,7 +37,8 @@ class Stats(ctypes.Structure):
                 ("flops_trsm_exec", ctypes.c_double), ("flops_syrk_exec", ctypes.c_double),
                 ("flops_dense", ctypes.c_double), ("bytes_assembly", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("n_supernodes", c_i64), ("n_trsm_tasks", c_i64),
-                ("n_syrk_tasks", c_i64), ("n_apply_tasks", c_i64), ("y_doubles", c_i64)]
+                ("n_syrk_tasks", c_i64), ("n_apply_tasks", c_i64), ("y_doubles", c_i64),
+                ("max_supernode", c_i64)]
 
 
 # every symbol include/sc.h declares, with (argtypes, restype)

@@ -31,7 +31,67 @@ void record(sc_ctx *ctx, int k, cudaStream_t st) {
 
 }  // namespace
 
-sc_ctx::~sc_ctx() { destroy_events(this); }
+sc_ctx::~sc_ctx() {
+  destroy_events(this);
+  for (auto &e : aux_done)
+    if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+  for (auto &s : aux_streams)
+    if (s) cudaStreamDestroy(static_cast<cudaStream_t>(s));
+  if (fork_event) cudaEventDestroy(static_cast<cudaEvent_t>(fork_event));
+}
+
+std::vector<int> sc_ctx::groups() const {
+  std::vector<int> g;
+  for (int v = 0; v < 8; ++v)
+    if (trsm_grp[v][1] > 0 || syrk_grp[v][1] > 0) g.push_back(v);
+  return g;
+}
+
+namespace sc {
+
+int launch_groups(sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, double *F, void *stream,
+                  bool aux) {
+  const std::vector<int> g = c.groups();
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!aux || g.size() <= 1) {
+    for (int v : g) {
+      int e = launch_group_trsm(c, v, Lv, invd, ws, Y, stream);
+      if (e) return e;
+    }
+    for (int v : g) {
+      int e = launch_group_syrk(c, v, Y, ws, F, stream);
+      if (e) return e;
+    }
+    return 0;
+  }
+  cudaError_t e;
+  if (!c.fork_event) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return (int)e;
+    c.fork_event = ev;
+  }
+  if ((e = cudaEventRecord(static_cast<cudaEvent_t>(c.fork_event), st)) != cudaSuccess) return (int)e;
+  for (int v : g) {
+    if (!c.aux_streams[v]) {
+      cudaStream_t s;
+      cudaEvent_t ev;
+      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return (int)e;
+      c.aux_streams[v] = s;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return (int)e;
+      c.aux_done[v] = ev;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(c.aux_streams[v]);
+    if ((e = cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(c.fork_event), 0)) != cudaSuccess) return (int)e;
+    int rc = launch_group_trsm(c, v, Lv, invd, ws, Y, s);
+    if (!rc) rc = launch_group_syrk(c, v, Y, ws, F, s);
+    if (rc) return rc;
+    if ((e = cudaEventRecord(static_cast<cudaEvent_t>(c.aux_done[v]), s)) != cudaSuccess) return (int)e;
+    if ((e = cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(c.aux_done[v]), 0)) != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
+}  // namespace sc
 
 extern "C" {
 
@@ -98,11 +158,18 @@ sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_d
   int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, ws, stream);
   if (rc) return cuda_fail(ctx, rc, "prep kernel launch");
   record(ctx, 1, st);
-  rc = launch_trsm(*ctx, L_values_dev, invd, ws, Y, stream);
-  if (rc) return cuda_fail(ctx, rc, "trsm kernel launch");
-  record(ctx, 2, st);
-  rc = launch_syrk(*ctx, Y, ws, F_dev, stream);
-  if (rc) return cuda_fail(ctx, rc, "syrk kernel launch");
+  const std::vector<int> g = ctx->groups();
+  if (g.size() == 1) {     // one variant: stage events around the TRSM and the SYRK
+    rc = launch_group_trsm(*ctx, g[0], L_values_dev, invd, ws, Y, stream);
+    if (rc) return cuda_fail(ctx, rc, "trsm kernel launch");
+    record(ctx, 2, st);
+    rc = launch_group_syrk(*ctx, g[0], Y, ws, F_dev, stream);
+    if (rc) return cuda_fail(ctx, rc, "syrk kernel launch");
+  } else {                 // several variants run concurrently; the TRSM stage covers both halves
+    rc = launch_groups(*ctx, L_values_dev, invd, ws, Y, F_dev, stream, true);
+    if (rc) return cuda_fail(ctx, rc, "variant group launch");
+    record(ctx, 2, st);
+  }
   record(ctx, 3, st);
   ctx->stage_recorded = ctx->stage_events[0] != nullptr;
   return SC_OK;

@@ -147,6 +147,9 @@ struct sc_ctx {
   size_t plan_dev_bytes = 0;
   void *stage_events[4] = {nullptr, nullptr, nullptr, nullptr};  // cudaEvent_t, stage timing
   bool stage_recorded = false;
+  // created on first use by a batch with several variant groups
+  void *aux_streams[8] = {}, *aux_done[8] = {}, *fork_event = nullptr;
+  std::vector<int> groups() const;   // variants present (0 = FP64, 3..7)
   ~sc_ctx();
 
   sc::PlanPtrs ptrs() const;
@@ -159,13 +162,20 @@ sc_status fail(sc_ctx *ctx, sc_status st, const std::string &msg);
 // kernel launchers (sc_kernels.cu); return cudaError_t as int
 int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F,
                 void *ws, void *stream);
-int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream);
-int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream);
+// one variant group (0 = FP64, 3..7 = digits): its TRSM half and its SYRK half
+int launch_group_trsm(const sc_ctx &c, int v, const double *Lv, const double *invd, void *ws, double *Y,
+                      void *stream);
+int launch_group_syrk(const sc_ctx &c, int v, const double *Y, void *ws, double *F, void *stream);
+// every variant group: one after the other on `stream`, or (aux != nullptr, several
+// groups) each on its own stream forked from and joined back into `stream`
+int launch_groups(sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, double *F, void *stream,
+                  bool aux);
 // split-precision launchers: one variant group (S digits, items [base, base + count))
 int launch_lpack_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, void *ws, void *stream);
 int launch_trsm_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, const double *invd,
                       void *ws, double *Y, void *stream);
-int launch_yslice_split(const sc_ctx &c, const double *Y, void *ws, void *stream);   // all split groups
+int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream);
+int launch_yslice_group(const sc_ctx &c, int S, const double *Y, void *ws, void *stream);
 int launch_syrk_split(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);

@@ -259,34 +259,38 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
   }
   if (c.nsub > 0) fpad_kernel<<<c.nsub, 128, 0, S(stream)>>>(p.subs, F);
   int e = (int)cudaGetLastError();
-  for (int v = 3; v < 8 && !e; ++v)
-    if (c.sblk_grp[v][1] > 0) e = launch_lpack_split(c, v, c.sblk_grp[v][0], c.sblk_grp[v][1], Lv, ws, stream);
+  if (!e && c.n_slices > 0) e = launch_colexp_reset(c, ws, stream);
   return e;
 }
 
-int launch_trsm(const sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, void *stream) {
-  if (c.trsm_grp[0][1] > 0) {
-    PlanPtrs p = c.ptrs();
-    p.trsm_tasks += c.trsm_grp[0][0];
-    trsm_kernel<<<(unsigned)c.trsm_grp[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
+// First half of one variant group's pipeline: (digit planes of L,) sparse TRSM.
+int launch_group_trsm(const sc_ctx &c, int v, const double *Lv, const double *invd, void *ws, double *Y,
+                      void *stream) {
+  if (v == 0) {
+    if (c.trsm_grp[0][1] > 0) {
+      PlanPtrs p = c.ptrs();
+      p.trsm_tasks += c.trsm_grp[0][0];
+      trsm_kernel<<<(unsigned)c.trsm_grp[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
+    }
+    return (int)cudaGetLastError();
   }
-  int e = (int)cudaGetLastError();
-  for (int v = 3; v < 8 && !e; ++v)
-    if (c.trsm_grp[v][1] > 0) e = launch_trsm_split(c, v, c.trsm_grp[v][0], c.trsm_grp[v][1], Lv, invd, ws, Y, stream);
+  int e = launch_lpack_split(c, v, c.sblk_grp[v][0], c.sblk_grp[v][1], Lv, ws, stream);
+  if (!e) e = launch_trsm_split(c, v, c.trsm_grp[v][0], c.trsm_grp[v][1], Lv, invd, ws, Y, stream);
   return e;
 }
 
-int launch_syrk(const sc_ctx &c, const double *Y, void *ws, double *F, void *stream) {
-  int e = 0;
-  if (c.n_slices > 0) e = launch_yslice_split(c, Y, ws, stream);
-  if (!e && c.syrk_grp[0][1] > 0) {
-    PlanPtrs p = c.ptrs();
-    p.syrk_tasks += c.syrk_grp[0][0];
-    syrk_kernel<<<(unsigned)c.syrk_grp[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
-    e = (int)cudaGetLastError();
+// Second half: (digit planes of Y,) pruned SYRK with the back permutation.
+int launch_group_syrk(const sc_ctx &c, int v, const double *Y, void *ws, double *F, void *stream) {
+  if (v == 0) {
+    if (c.syrk_grp[0][1] > 0) {
+      PlanPtrs p = c.ptrs();
+      p.syrk_tasks += c.syrk_grp[0][0];
+      syrk_kernel<<<(unsigned)c.syrk_grp[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
+    }
+    return (int)cudaGetLastError();
   }
-  for (int v = 3; v < 8 && !e; ++v)
-    if (c.syrk_grp[v][1] > 0) e = launch_syrk_split(c, v, c.syrk_grp[v][0], c.syrk_grp[v][1], ws, F, stream);
+  int e = launch_yslice_group(c, v, Y, ws, stream);
+  if (!e) e = launch_syrk_split(c, v, c.syrk_grp[v][0], c.syrk_grp[v][1], ws, F, stream);
   return e;
 }
 

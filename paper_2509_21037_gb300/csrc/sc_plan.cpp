@@ -295,6 +295,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
         }
       }
       sns.push_back(sn);
+      st.max_supernode = std::max<int64_t>(st.max_supernode, sn.ns);
       for (int32_t c = 0; c < sn.ns; ++c) active_cols.push_back(sn.lcp_off + c);
     }
     // pruned-row targets

@@ -483,33 +483,27 @@ int launch_trsm_split(const sc_ctx &c, int S_, int64_t base, int64_t count, cons
   return (int)cudaGetLastError();
 }
 
-int launch_yslice_split(const sc_ctx &c, const double *Y, void *ws, void *stream) {
+int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream) {
+  int64_t ncols = 0;
+  for (int32_t m : c.m) ncols += m;
+  if (ncols <= 0) return 0;
+  uint8_t *w = static_cast<uint8_t *>(ws);
+  return (int)cudaMemsetAsync(w + c.ws.colexp_off, 0, sizeof(int) * (size_t)ncols, static_cast<cudaStream_t>(stream));
+}
+
+int launch_yslice_group(const sc_ctx &c, int S_, const double *Y, void *ws, void *stream) {
+  const int64_t base = c.sblk_grp[S_][0], count = c.sblk_grp[S_][1];
+  if (count <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
   int *colexp = reinterpret_cast<int *>(w + c.ws.colexp_off);
   __nv_bfloat16 *Yd = reinterpret_cast<__nv_bfloat16 *>(w + c.ws.yd_off);
-  int64_t ncols = 0;
-  for (int32_t m : c.m) ncols += m;
-  if (ncols > 0) {
-    cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)ncols, st);
-    if (e != cudaSuccess) return (int)e;
-  }
-  for (int v = 3; v < 8; ++v) {
-    const int64_t base = c.sblk_grp[v][0], count = c.sblk_grp[v][1];
-    if (count <= 0) continue;
-    PlanPtrs p = c.ptrs();
-    p.sblk += 2 * base;
-    ycolexp_kernel<<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp);
-  }
-  for (int v = 3; v < 8; ++v) {
-    const int64_t base = c.sblk_grp[v][0], count = c.sblk_grp[v][1];
-    if (count <= 0) continue;
-    PlanPtrs p = c.ptrs();
-    p.sblk += 2 * base;
+  PlanPtrs p = c.ptrs();
+  p.sblk += 2 * base;
+  ycolexp_kernel<<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp);
 #define YS(S) yslice_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
-    SC_SPLIT_SWITCH(v, YS)
+  SC_SPLIT_SWITCH(S_, YS)
 #undef YS
-  }
   return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,71 @@
+"""Autotuner and learned variant selector on a mixed 2D heat / 3D elasticity
+batch: the MLP, trained on the autotuner's records of half of the subdomain
+classes, picks variants for the other half; the autotuner's own measurements
+there judge its regret; the selected batch must beat the FP64-only batch and
+meet the error target."""
+import numpy as np
+import pytest
+
+import synth
+from paper_2509_21037_gb300 import host, sc, tune
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _batch_ms(fs, n_dual, dev, var, reps=3):
+    plan = sc.Plan(fs, n_dual, sub_slices=var).upload(dev)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    F = plan.new_F(dev)
+    plan.assemble(Lv, F)
+    assert plan.device_status() == 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        plan.assemble(Lv, F)
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def test_learned_selector_gain_and_regret(dev):
+    prob = synth.mixed_batch(lat2d=(6, 6), k2d=(12, 48), lat3d=(4, 3, 2), k3d=(3, 9), seed=3)
+    fs = host.factorize_problem(prob.subdomains)
+    V = (0, 7, 5, 4)
+    recs = tune.autotune(fs, dev, variants=V, reps=2)
+    for k in sorted(recs, key=lambda k: recs[k].features[0]):
+        r = recs[k]
+        print(f"n={k[0]:6d} m={k[1]:5d} " + " ".join(f"v{v}:{r.time_ms[v] * 1e3:8.1f}us/{r.error[v]:.0e}" for v in V))
+    keys = sorted(recs, key=lambda k: (recs[k].features[0], k[:3]))
+    train, held = keys[::2], keys[1::2]
+    sel = tune.LearnedSelector(variants=V, device=dev, seed=0)
+    hist = sel.fit([recs[k] for k in train], epochs=3000)
+    assert hist[-1] < 0.2 * hist[0]
+    tol = 1e-8
+    regrets, feasible = [], []
+    for k in held:
+        ch = sel.choose(recs[k].features[None], tol)[0]
+        best = tune.best_variant(recs[k].time_ms, recs[k].error, tol)
+        regrets.append(recs[k].time_ms[ch] / recs[k].time_ms[best] - 1.0)
+        feasible.append(ch == 0 or recs[k].error[ch] <= tol)
+    print(f"held-out classes {len(held)}: mean regret {np.mean(regrets):.3f}, max {np.max(regrets):.3f}, "
+          f"feasible {np.mean(feasible):.2f}")
+    assert all(feasible)
+    assert np.mean(regrets) < 0.25
+    var = tune.select(fs, tol, sel, measured={k: recs[k] for k in train})
+    t_sel = _batch_ms(fs, prob.n_dual, dev, var)
+    t_fp64 = _batch_ms(fs, prob.n_dual, dev, [0] * len(fs))
+    t_s7 = _batch_ms(fs, prob.n_dual, dev, [7] * len(fs))
+    t_s5 = _batch_ms(fs, prob.n_dual, dev, [5] * len(fs))
+    print(f"batch ms: selected {t_sel:.2f}, all FP64 {t_fp64:.2f}, all 7-digit {t_s7:.2f}, all 5-digit {t_s5:.2f}; "
+          f"variants "
+          f"{dict(zip(*np.unique(var, return_counts=True)))}")
+    assert t_sel < t_fp64
+    assert t_sel <= 1.05 * min(t_s5, t_s7)        # no worse than the best uniform choice
