@@ -110,11 +110,18 @@ enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
  *            library-owned streams forked from and joined back into the
  *            caller's stream with events (the call stays asynchronous and
  *            ordered on the caller's stream). */
+/* ws_limit: 0, or an upper bound in bytes for the workspace.  The subdomains
+ *            (in their order) are then packed into waves whose temporary data
+ *            (Y and, for split precision, the digit planes) fit the bound;
+ *            waves run one after the other and reuse the same workspace (the
+ *            paper's temporary memory pool, Sec. 3.1).  SC_ERR_OOM if one
+ *            subdomain alone does not fit. */
 typedef struct {
   int32_t precision;
   int32_t n_slices;
   const int8_t *sub_slices;
-  int32_t reserved[4]; /* must be zero */
+  int64_t ws_limit;
+  int32_t reserved[2]; /* must be zero */
 } sc_options;
 
 typedef struct {
@@ -137,8 +144,9 @@ typedef struct {
   double bytes_apply;       /* algorithmic bytes of sc_apply: 8 m(m+1)/2 + 16 m per subdomain */
   int64_t n_supernodes;     /* active supernodes (touched by some column) */
   int64_t n_trsm_tasks, n_syrk_tasks, n_apply_tasks;
-  int64_t y_doubles;        /* workspace doubles of the sparse Y */
+  int64_t y_doubles;        /* workspace doubles of the sparse Y (all waves) */
   int64_t max_supernode;    /* columns of the largest active supernode */
+  int64_t n_waves;          /* workspace waves (1 without ws_limit) */
 } sc_stats;
 
 /* ---- initialization -------------------------------------------------------- */

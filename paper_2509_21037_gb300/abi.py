@@ -24,7 +24,8 @@ SC_FP64, SC_SPLIT_BF16 = 0, 1
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("sub_slices", c_vp), ("reserved", c_i32 * 4)]
+    _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("sub_slices", c_vp), ("ws_limit", c_i64),
+                ("reserved", c_i32 * 2)]
 
 
 class Sizes(ctypes.Structure):
@@ -38,7 +39,7 @@ class Stats(ctypes.Structure):
                 ("flops_dense", ctypes.c_double), ("bytes_assembly", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("n_supernodes", c_i64), ("n_trsm_tasks", c_i64),
                 ("n_syrk_tasks", c_i64), ("n_apply_tasks", c_i64), ("y_doubles", c_i64),
-                ("max_supernode", c_i64)]
+                ("max_supernode", c_i64), ("n_waves", c_i64)]
 
 
 # every symbol include/sc.h declares, with (argtypes, restype)

@@ -40,26 +40,26 @@ sc_ctx::~sc_ctx() {
   if (fork_event) cudaEventDestroy(static_cast<cudaEvent_t>(fork_event));
 }
 
-std::vector<int> sc_ctx::groups() const {
+std::vector<int> sc_ctx::groups(int w) const {
   std::vector<int> g;
   for (int v = 0; v < 8; ++v)
-    if (trsm_grp[v][1] > 0 || syrk_grp[v][1] > 0) g.push_back(v);
+    if (waves[w].trsm[v][1] > 0 || waves[w].syrk[v][1] > 0) g.push_back(v);
   return g;
 }
 
 namespace sc {
 
-int launch_groups(sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, double *F, void *stream,
-                  bool aux) {
-  const std::vector<int> g = c.groups();
+int launch_groups(sc_ctx &c, int w, const double *Lv, const double *invd, void *ws, double *Y, double *F,
+                  void *stream, bool aux) {
+  const std::vector<int> g = c.groups(w);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!aux || g.size() <= 1) {
     for (int v : g) {
-      int e = launch_group_trsm(c, v, Lv, invd, ws, Y, stream);
+      int e = launch_group_trsm(c, w, v, Lv, invd, ws, Y, stream);
       if (e) return e;
     }
     for (int v : g) {
-      int e = launch_group_syrk(c, v, Y, ws, F, stream);
+      int e = launch_group_syrk(c, w, v, Y, ws, F, stream);
       if (e) return e;
     }
     return 0;
@@ -82,8 +82,8 @@ int launch_groups(sc_ctx &c, const double *Lv, const double *invd, void *ws, dou
     }
     cudaStream_t s = static_cast<cudaStream_t>(c.aux_streams[v]);
     if ((e = cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(c.fork_event), 0)) != cudaSuccess) return (int)e;
-    int rc = launch_group_trsm(c, v, Lv, invd, ws, Y, s);
-    if (!rc) rc = launch_group_syrk(c, v, Y, ws, F, s);
+    int rc = launch_group_trsm(c, w, v, Lv, invd, ws, Y, s);
+    if (!rc) rc = launch_group_syrk(c, w, v, Y, ws, F, s);
     if (rc) return rc;
     if ((e = cudaEventRecord(static_cast<cudaEvent_t>(c.aux_done[v]), s)) != cudaSuccess) return (int)e;
     if ((e = cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(c.aux_done[v]), 0)) != cudaSuccess) return (int)e;
@@ -158,16 +158,18 @@ sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_d
   int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, ws, stream);
   if (rc) return cuda_fail(ctx, rc, "prep kernel launch");
   record(ctx, 1, st);
-  const std::vector<int> g = ctx->groups();
-  if (g.size() == 1) {     // one variant: stage events around the TRSM and the SYRK
-    rc = launch_group_trsm(*ctx, g[0], L_values_dev, invd, ws, Y, stream);
+  const std::vector<int> g0 = ctx->waves.empty() ? std::vector<int>() : ctx->groups(0);
+  if (ctx->waves.size() == 1 && g0.size() == 1) {   // one wave, one variant: events around TRSM and SYRK
+    rc = launch_group_trsm(*ctx, 0, g0[0], L_values_dev, invd, ws, Y, stream);
     if (rc) return cuda_fail(ctx, rc, "trsm kernel launch");
     record(ctx, 2, st);
-    rc = launch_group_syrk(*ctx, g[0], Y, ws, F_dev, stream);
+    rc = launch_group_syrk(*ctx, 0, g0[0], Y, ws, F_dev, stream);
     if (rc) return cuda_fail(ctx, rc, "syrk kernel launch");
-  } else {                 // several variants run concurrently; the TRSM stage covers both halves
-    rc = launch_groups(*ctx, L_values_dev, invd, ws, Y, F_dev, stream, true);
-    if (rc) return cuda_fail(ctx, rc, "variant group launch");
+  } else {                 // waves in order, variants of a wave concurrently; stage [1] covers all
+    for (int w = 0; w < (int)ctx->waves.size(); ++w) {
+      rc = launch_groups(*ctx, w, L_values_dev, invd, ws, Y, F_dev, stream, true);
+      if (rc) return cuda_fail(ctx, rc, "variant group launch");
+    }
     record(ctx, 2, st);
   }
   record(ctx, 3, st);

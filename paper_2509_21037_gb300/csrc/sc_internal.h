@@ -129,8 +129,13 @@ struct sc_ctx {
   int32_t precision = SC_FP64;       // SC_SPLIT_BF16 when any subdomain runs split
   int32_t n_slices = 0;              // largest digit count of any subdomain (plane sizing)
   std::vector<int8_t> sub_var;       // per subdomain: 0 = FP64, 3..7 = split digits
-  // launch groups by variant (index 0 = FP64, 3..7 = digits): first item, count
-  int64_t trsm_grp[8][2] = {}, syrk_grp[8][2] = {}, sblk_grp[8][2] = {};
+  int64_t ws_limit = 0;              // workspace bytes per wave (0 = one wave)
+  // per wave, launch groups by variant (index 0 = FP64, 3..7 = digits): first item, count
+  struct WaveGroups {
+    int64_t trsm[8][2] = {}, syrk[8][2] = {}, sblk[8][2] = {};
+  };
+  std::vector<WaveGroups> waves;
+  std::vector<int32_t> sub_wave;     // wave of every subdomain
   int32_t nsub = 0;
   int64_t n_dual = 0;
   std::vector<uint8_t> blob;     // plan tables, 256-byte aligned sections
@@ -149,7 +154,7 @@ struct sc_ctx {
   bool stage_recorded = false;
   // created on first use by a batch with several variant groups
   void *aux_streams[8] = {}, *aux_done[8] = {}, *fork_event = nullptr;
-  std::vector<int> groups() const;   // variants present (0 = FP64, 3..7)
+  std::vector<int> groups(int w) const;   // variants present in wave w (0 = FP64, 3..7)
   ~sc_ctx();
 
   sc::PlanPtrs ptrs() const;
@@ -162,20 +167,21 @@ sc_status fail(sc_ctx *ctx, sc_status st, const std::string &msg);
 // kernel launchers (sc_kernels.cu); return cudaError_t as int
 int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F,
                 void *ws, void *stream);
-// one variant group (0 = FP64, 3..7 = digits): its TRSM half and its SYRK half
-int launch_group_trsm(const sc_ctx &c, int v, const double *Lv, const double *invd, void *ws, double *Y,
+// one variant group (0 = FP64, 3..7 = digits) of wave w: its TRSM half and its SYRK half
+int launch_group_trsm(const sc_ctx &c, int w, int v, const double *Lv, const double *invd, void *ws, double *Y,
                       void *stream);
-int launch_group_syrk(const sc_ctx &c, int v, const double *Y, void *ws, double *F, void *stream);
-// every variant group: one after the other on `stream`, or (aux != nullptr, several
+int launch_group_syrk(const sc_ctx &c, int w, int v, const double *Y, void *ws, double *F, void *stream);
+// every variant group of wave w: one after the other on `stream`, or (aux, several
 // groups) each on its own stream forked from and joined back into `stream`
-int launch_groups(sc_ctx &c, const double *Lv, const double *invd, void *ws, double *Y, double *F, void *stream,
-                  bool aux);
-// split-precision launchers: one variant group (S digits, items [base, base + count))
+int launch_groups(sc_ctx &c, int w, const double *Lv, const double *invd, void *ws, double *Y, double *F,
+                  void *stream, bool aux);
+// split-precision launchers: one variant group of one wave (S digits, items [base, base + count))
 int launch_lpack_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, void *ws, void *stream);
 int launch_trsm_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, const double *invd,
                       void *ws, double *Y, void *stream);
 int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream);
-int launch_yslice_group(const sc_ctx &c, int S, const double *Y, void *ws, void *stream);
+int launch_yslice_group(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Y, void *ws,
+                        void *stream);
 int launch_syrk_split(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);

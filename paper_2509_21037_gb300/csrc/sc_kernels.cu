@@ -264,33 +264,35 @@ int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *statu
 }
 
 // First half of one variant group's pipeline: (digit planes of L,) sparse TRSM.
-int launch_group_trsm(const sc_ctx &c, int v, const double *Lv, const double *invd, void *ws, double *Y,
+int launch_group_trsm(const sc_ctx &c, int w, int v, const double *Lv, const double *invd, void *ws, double *Y,
                       void *stream) {
+  const auto &G = c.waves[w];
   if (v == 0) {
-    if (c.trsm_grp[0][1] > 0) {
+    if (G.trsm[0][1] > 0) {
       PlanPtrs p = c.ptrs();
-      p.trsm_tasks += c.trsm_grp[0][0];
-      trsm_kernel<<<(unsigned)c.trsm_grp[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
+      p.trsm_tasks += G.trsm[0][0];
+      trsm_kernel<<<(unsigned)G.trsm[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
     }
     return (int)cudaGetLastError();
   }
-  int e = launch_lpack_split(c, v, c.sblk_grp[v][0], c.sblk_grp[v][1], Lv, ws, stream);
-  if (!e) e = launch_trsm_split(c, v, c.trsm_grp[v][0], c.trsm_grp[v][1], Lv, invd, ws, Y, stream);
+  int e = launch_lpack_split(c, v, G.sblk[v][0], G.sblk[v][1], Lv, ws, stream);
+  if (!e) e = launch_trsm_split(c, v, G.trsm[v][0], G.trsm[v][1], Lv, invd, ws, Y, stream);
   return e;
 }
 
 // Second half: (digit planes of Y,) pruned SYRK with the back permutation.
-int launch_group_syrk(const sc_ctx &c, int v, const double *Y, void *ws, double *F, void *stream) {
+int launch_group_syrk(const sc_ctx &c, int w, int v, const double *Y, void *ws, double *F, void *stream) {
+  const auto &G = c.waves[w];
   if (v == 0) {
-    if (c.syrk_grp[0][1] > 0) {
+    if (G.syrk[0][1] > 0) {
       PlanPtrs p = c.ptrs();
-      p.syrk_tasks += c.syrk_grp[0][0];
-      syrk_kernel<<<(unsigned)c.syrk_grp[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
+      p.syrk_tasks += G.syrk[0][0];
+      syrk_kernel<<<(unsigned)G.syrk[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
     }
     return (int)cudaGetLastError();
   }
-  int e = launch_yslice_group(c, v, Y, ws, stream);
-  if (!e) e = launch_syrk_split(c, v, c.syrk_grp[v][0], c.syrk_grp[v][1], ws, F, stream);
+  int e = launch_yslice_group(c, v, G.sblk[v][0], G.sblk[v][1], Y, ws, stream);
+  if (!e) e = launch_syrk_split(c, v, G.syrk[v][0], G.syrk[v][1], ws, F, stream);
   return e;
 }
 

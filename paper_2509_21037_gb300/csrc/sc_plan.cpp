@@ -229,15 +229,48 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<ApplyTask> apply;
   std::vector<int32_t> active_cols;
   std::vector<int32_t> cuts;
-  std::vector<int32_t> sblk_v[8];
+  std::vector<int32_t> sblk_v[8], sblk_w[8];
   std::vector<double> trsm_cost, syrk_cost;
   std::vector<int8_t> trsm_var, syrk_var;
+  std::vector<int32_t> trsm_wave, syrk_wave;
+
+  // temporary data of each subdomain and its packing into waves
+  ctx->sub_wave.assign(nsub, 0);
+  {
+    const double Smax = ctx->n_slices;
+    double cur = 0.0;
+    int32_t w = 0;
+    bool any = false;
+    for (int32_t i = 0; i < nsub; ++i) {
+      const SubPlan &S = P[i];
+      double y = 0, yd = 0, ld = 0;
+      for (size_t s = 0; s < S.sn_c0.size(); ++s) {
+        const double ws = S.sn_jhi[s] - S.sn_jlo[s];
+        if (ws <= 0) continue;
+        y += S.sn_ns[s] * ws;
+        yd += ws * ((S.sn_ns[s] + 31) / 32 * 32);
+        for (int32_t kb = 0; kb < S.sn_ns[s]; kb += 32) ld += S.sn_ns[s] + S.sn_rs[s] - kb - std::min(32, S.sn_ns[s] - kb);
+      }
+      const double need = 8.0 * y + (ctx->sub_var[i] ? Smax * (2.0 * yd + 64.0 * ld) + 2.0 * ld : 0.0) + 4096.0;
+      if (ctx->ws_limit > 0) {
+        if (need > (double)ctx->ws_limit)
+          return fail(ctx, SC_ERR_OOM, sub_msg(i, "needs " + std::to_string((int64_t)need) +
+                                                      " workspace bytes, more than ws_limit"));
+        if (any && cur + need > (double)ctx->ws_limit) { ++w; cur = 0.0; }
+      }
+      cur += need;
+      any = true;
+      ctx->sub_wave[i] = w;
+    }
+    ctx->waves.assign((size_t)w + 1, sc_ctx::WaveGroups());
+  }
 
   ctx->F_offsets.assign(nsub + 1, 0);
   ctx->L_offsets.assign(nsub + 1, 0);
   ctx->n.resize(nsub);
   ctx->m.resize(nsub);
   int64_t y_total = 0, col_total = 0, lcp_total = 0, ld_rows_total = 0, yd_total = 0;
+  int64_t y_max = 0, ld_max = 0, yd_max = 0, y_all = 0;  // per-wave offsets restart at 0
   sc_stats st{};
   int32_t max_m = 0;
 
@@ -245,6 +278,10 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     const sc_subdomain_desc &D = d[i];
     SubPlan &S = P[i];
     const int32_t n = D.n, m = D.m, nt = (m + kTile - 1) / kTile;
+    if (i > 0 && ctx->sub_wave[i] != ctx->sub_wave[i - 1]) {   // a new wave reuses the workspace
+      y_all += y_total;
+      y_total = ld_rows_total = yd_total = 0;
+    }
     ctx->n[i] = n;
     ctx->m[i] = m;
     max_m = std::max(max_m, m);
@@ -292,9 +329,13 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
         if (var) {
           sblk_v[var].push_back((int32_t)sns.size());
           sblk_v[var].push_back(kb / 32);
+          sblk_w[var].push_back(ctx->sub_wave[i]);
         }
       }
       sns.push_back(sn);
+      y_max = std::max(y_max, y_total);
+      ld_max = std::max(ld_max, ld_rows_total);
+      yd_max = std::max(yd_max, yd_total);
       st.max_supernode = std::max<int64_t>(st.max_supernode, sn.ns);
       for (int32_t c = 0; c < sn.ns; ++c) active_cols.push_back(sn.lcp_off + c);
     }
@@ -367,6 +408,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       trsm.push_back(t);
       trsm_cost.push_back(exec + 1e3 * t.list_len);
       trsm_var.push_back(ctx->sub_var[i]);
+      trsm_wave.push_back(ctx->sub_wave[i]);
     }
     // chunk-pair lists (lower triangle of sorted chunks)
     for (int32_t q1 = 0; q1 < nchunk; ++q1) {
@@ -393,6 +435,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
         syrk.push_back(t);
         syrk_cost.push_back(exec + 1e3 * (t.list_len + 1));
         syrk_var.push_back(ctx->sub_var[i]);
+        syrk_wave.push_back(ctx->sub_wave[i]);
       }
     }
     for (int32_t s = 0; s < nsn; ++s) {
@@ -411,43 +454,53 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     col_total += m;
     lcp_total += n;
   }
-  // grouped by variant (one launch per group), largest tasks first inside a
-  // group: the block scheduler hands out CTAs roughly in index order
-  auto order_by = [](const std::vector<double> &cost, const std::vector<int8_t> &var) {
+  // grouped by wave and variant (one launch per group), largest tasks first
+  // inside a group: the block scheduler hands out CTAs roughly in index order
+  auto order_by = [](const std::vector<double> &cost, const std::vector<int8_t> &var,
+                     const std::vector<int32_t> &wave) {
     std::vector<int32_t> o(cost.size());
     std::iota(o.begin(), o.end(), 0);
     std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) {
+      if (wave[a] != wave[b]) return wave[a] < wave[b];
       return var[a] != var[b] ? var[a] < var[b] : cost[a] > cost[b];
     });
     return o;
   };
-  auto groups = [](const std::vector<int8_t> &var, const std::vector<int32_t> &o, int64_t (&grp)[8][2]) {
-    for (auto &g : grp) g[0] = g[1] = 0;
+  auto groups = [&](const std::vector<int8_t> &var, const std::vector<int32_t> &wave, const std::vector<int32_t> &o,
+                    int which) {
     for (size_t k = 0; k < o.size(); ++k) {
       const int v = var[o[k]];
-      if (grp[v][1] == 0) grp[v][0] = (int64_t)k;
-      grp[v][1]++;
+      auto &g = which == 0 ? ctx->waves[wave[o[k]]].trsm[v] : ctx->waves[wave[o[k]]].syrk[v];
+      if (g[1] == 0) g[0] = (int64_t)k;
+      g[1]++;
     }
   };
   {
-    auto o = order_by(trsm_cost, trsm_var);
-    groups(trsm_var, o, ctx->trsm_grp);
+    auto o = order_by(trsm_cost, trsm_var, trsm_wave);
+    groups(trsm_var, trsm_wave, o, 0);
     std::vector<TrsmTask> t2(trsm.size());
     for (size_t k = 0; k < o.size(); ++k) t2[k] = trsm[o[k]];
     trsm.swap(t2);
   }
   {
-    auto o = order_by(syrk_cost, syrk_var);
-    groups(syrk_var, o, ctx->syrk_grp);
+    auto o = order_by(syrk_cost, syrk_var, syrk_wave);
+    groups(syrk_var, syrk_wave, o, 1);
     std::vector<SyrkTask> t2(syrk.size());
     for (size_t k = 0; k < o.size(); ++k) t2[k] = syrk[o[k]];
     syrk.swap(t2);
   }
   std::vector<int32_t> sblk;
-  for (int v = 0; v < 8; ++v) {
-    ctx->sblk_grp[v][0] = (int64_t)sblk.size() / 2;
-    ctx->sblk_grp[v][1] = (int64_t)sblk_v[v].size() / 2;
-    sblk.insert(sblk.end(), sblk_v[v].begin(), sblk_v[v].end());
+  for (size_t w = 0; w < ctx->waves.size(); ++w) {
+    for (int v = 0; v < 8; ++v) {
+      auto &g = ctx->waves[w].sblk[v];
+      g[0] = (int64_t)sblk.size() / 2;
+      for (size_t k = 0; k < sblk_w[v].size(); ++k) {
+        if (sblk_w[v][k] != (int32_t)w) continue;
+        sblk.push_back(sblk_v[v][2 * k]);
+        sblk.push_back(sblk_v[v][2 * k + 1]);
+      }
+      g[1] = (int64_t)sblk.size() / 2 - g[0];
+    }
   }
   ctx->blob.assign(kHeaderBytes, 0);
   add_section(ctx->blob, ctx->s_subs, subs);
@@ -492,17 +545,17 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   ctx->ws.status_off = 0;
   ctx->ws.invd_off = 256;
   ctx->ws.y_off = (ctx->ws.invd_off + sizeof(double) * (size_t)lcp_total + 255) & ~size_t(255);
-  ctx->ws.total = ctx->ws.y_off + sizeof(double) * (size_t)y_total;
+  ctx->ws.total = ctx->ws.y_off + sizeof(double) * (size_t)y_max;
   if (ctx->n_slices > 0) {
     const size_t S = (size_t)ctx->n_slices;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     ctx->ws.colexp_off = up(ctx->ws.total);
     ctx->ws.yd_off = up(ctx->ws.colexp_off + sizeof(int32_t) * (size_t)col_total);
-    ctx->ws.yd_plane = yd_total;
-    ctx->ws.ld_off = up(ctx->ws.yd_off + 2 * S * (size_t)yd_total);
-    ctx->ws.ld_rows = ld_rows_total;
-    ctx->ws.lexp_off = up(ctx->ws.ld_off + 2 * 32 * S * (size_t)ld_rows_total);
-    ctx->ws.total = up(ctx->ws.lexp_off + sizeof(int16_t) * (size_t)ld_rows_total);
+    ctx->ws.yd_plane = yd_max;
+    ctx->ws.ld_off = up(ctx->ws.yd_off + 2 * S * (size_t)yd_max);
+    ctx->ws.ld_rows = ld_max;
+    ctx->ws.lexp_off = up(ctx->ws.ld_off + 2 * 32 * S * (size_t)ld_max);
+    ctx->ws.total = up(ctx->ws.lexp_off + sizeof(int16_t) * (size_t)ld_max);
   }
 
   ctx->sizes.plan_bytes = ctx->blob.size();
@@ -516,7 +569,8 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   st.n_trsm_tasks = ctx->n_trsm;
   st.n_syrk_tasks = ctx->n_syrk;
   st.n_apply_tasks = ctx->n_apply;
-  st.y_doubles = y_total;
+  st.y_doubles = y_all + y_total;
+  st.n_waves = (int64_t)ctx->waves.size();
   ctx->stats = st;
   return SC_OK;
 }
@@ -571,6 +625,8 @@ sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomain
     }
     for (int8_t v : ctx->sub_var) ctx->n_slices = std::max<int32_t>(ctx->n_slices, v);
     ctx->precision = ctx->n_slices > 0 ? SC_SPLIT_BF16 : SC_FP64;
+    if (opt && opt->ws_limit < 0) st = fail(ctx, SC_ERR_INVALID_ARG, "ws_limit < 0");
+    ctx->ws_limit = opt ? opt->ws_limit : 0;
   }
   if (st == SC_OK && !(nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0)) {
     ctx->nsub = nsub;

@@ -491,8 +491,8 @@ int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream) {
   return (int)cudaMemsetAsync(w + c.ws.colexp_off, 0, sizeof(int) * (size_t)ncols, static_cast<cudaStream_t>(stream));
 }
 
-int launch_yslice_group(const sc_ctx &c, int S_, const double *Y, void *ws, void *stream) {
-  const int64_t base = c.sblk_grp[S_][0], count = c.sblk_grp[S_][1];
+int launch_yslice_group(const sc_ctx &c, int S_, int64_t base, int64_t count, const double *Y, void *ws,
+                        void *stream) {
   if (count <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);

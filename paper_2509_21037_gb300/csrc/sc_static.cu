@@ -81,7 +81,8 @@ extern "C" sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_value
   if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: status reset");
   int rc = launch_prep(*ctx, L_values_dev, invd, status, F_dev, ws, stream);
   if (rc) return static_fail(ctx, (cudaError_t)rc, "prep kernel launch");
-  rc = launch_groups(*ctx, L_values_dev, invd, ws, Y, F_dev, stream, false);   // no extra streams
+  for (int w = 0; w < (int)ctx->waves.size() && !rc; ++w)
+    rc = launch_groups(*ctx, w, L_values_dev, invd, ws, Y, F_dev, stream, false);   // no extra streams
   if (rc) return static_fail(ctx, (cudaError_t)rc, "assembly kernel launch");
   // report this call's device status (the caller has no handle on the scratch)
   uint32_t h = 0;

@@ -39,8 +39,10 @@ def _log2(x: float) -> float:
 
 
 def class_key(f) -> tuple:
-    """Subdomains with equal keys have identical patterns (and so identical plans)."""
-    return (f.n, f.m, f.L.nnz, hash(f.L.rowind.tobytes()), hash(f.bt_rowind.tobytes()))
+    """Structural class: the same factor pattern (n, nnz(L) and its row
+    indices) and a multiplier count in the same quarter-octave; the finer
+    differences (which dofs are glued) are left to the learned features."""
+    return (f.n, f.L.nnz, int(round(4 * math.log2(max(f.m, 1)))), hash(f.L.rowind.tobytes()))
 
 
 def subdomain_features(fs: Sequence) -> np.ndarray:
@@ -121,8 +123,9 @@ def autotune(fs: Sequence, device, variants=VARIANTS, classes: Optional[Sequence
     for k, mem in groups.items():
         if classes is not None and k not in classes:
             continue
-        t, e = measure_class(fs[mem[0]], device, variants, reps)
-        out[k] = ClassRecord(k, mem, feats[mem[0]], t, e)
+        rep = mem[len(mem) // 2]                      # a middle member represents the class
+        t, e = measure_class(fs[rep], device, variants, reps)
+        out[k] = ClassRecord(k, mem, feats[rep], t, e)
     return out
 
 

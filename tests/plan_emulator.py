@@ -51,7 +51,9 @@ def check_bounds(T: dict, sizes, stats) -> None:
     """Every address the kernels form, against the buffer it indexes."""
     subs, sns = T["subs"], T["sns"]
     ncols = int(T["header"]["n_cols"])
-    ydbl = int(stats.y_doubles)
+    # Y offsets restart in every workspace wave: the region holds the largest wave
+    ydbl = int(max([int(s["y_off"]) + int(s["ns"]) * int(s["jhi"] - s["jlo"]) for s in sns], default=0))
+    assert ydbl <= int(stats.y_doubles)
     Lvals = int(sizes.L_values)
     Fd = int(sizes.F_doubles)
     assert T["ws"][2] + 8 * ydbl <= sizes.ws_bytes
@@ -218,6 +220,7 @@ def export_dense(T: dict, F: np.ndarray, i: int) -> np.ndarray:
 
 
 def check_split_layout(T: dict, sizes, stats, sub_var=None) -> dict:
+    assert stats.n_waves == 1, "layout check covers single-wave plans"
     """Split-precision regions: per-supernode L digit rows (closed-form block
     bases against the prefix sums) and Y digit blocks (rows padded to 32) of
     the split subdomains are disjoint, in range and 16-byte aligned for the

@@ -225,3 +225,19 @@ def test_mlp_header_symbols_exported():
     names = _declared("sc_mlp.h")
     lib = _native.sc_lib()
     assert names and all(hasattr(lib, n) for n in names)
+
+
+def test_workspace_waves_bound_the_workspace():
+    """ws_limit packs subdomains into waves that reuse one workspace."""
+    prob = synth.cube_heat_3d(2, 5)
+    fs = host.factorize_problem(prob.subdomains)
+    one = sc.Plan(fs, prob.n_dual)
+    lim = one.sizes.ws_bytes // 3
+    waved = sc.Plan(fs, prob.n_dual, ws_limit=lim)
+    assert waved.stats.n_waves >= 3 and waved.sizes.ws_bytes <= lim
+    assert waved.stats.y_doubles == one.stats.y_doubles
+    T = pe.export_plan(waved)
+    pe.check_bounds(T, waved.sizes, waved.stats)
+    with pytest.raises(sc.SCError) as e:
+        sc.Plan(fs, prob.n_dual, ws_limit=1000)
+    assert e.value.status == abi.SC_ERR_OOM

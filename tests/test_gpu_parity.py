@@ -291,3 +291,24 @@ def test_config3_full_size_sampled(dev):
               f"kernel error vs exact-with-L {oracle.relative_frobenius(Fg, FL):.3e}")
         assert err <= floor + TOL
         assert oracle.relative_frobenius(Fg, FL) <= TOL
+
+
+@pytest.mark.parametrize("split", [0, 5])
+def test_workspace_waves_match_single_wave(dev, split):
+    """A workspace bound splits the batch into waves reusing one workspace;
+    the result equals the single-wave assembly bit for bit."""
+    prob = synth.cube_heat_3d(parts=2, k=6, coef_seed=2)
+    fs = host.factorize_problem(prob.subdomains)
+    var = [split] * len(fs)
+    ref_plan, F_ref, Lv = None, None, None
+    ref_plan = sc.Plan(fs, prob.n_dual, sub_slices=var).upload(dev)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    F_ref = ref_plan.new_F(dev)
+    ref_plan.assemble(Lv, F_ref)
+    plan = sc.Plan(fs, prob.n_dual, sub_slices=var, ws_limit=ref_plan.sizes.ws_bytes // 3).upload(dev)
+    assert plan.stats.n_waves >= 3
+    F = plan.new_F(dev)
+    F.fill_(float("nan"))
+    plan.assemble(Lv, F)
+    assert plan.device_status() == abi.SC_OK
+    assert torch.equal(F, F_ref)

@@ -42,8 +42,8 @@ def test_learned_selector_gain_and_regret(dev):
     recs = tune.autotune(fs, dev, variants=V, reps=2)
     for k in sorted(recs, key=lambda k: recs[k].features[0]):
         r = recs[k]
-        print(f"n={k[0]:6d} m={k[1]:5d} " + " ".join(f"v{v}:{r.time_ms[v] * 1e3:8.1f}us/{r.error[v]:.0e}" for v in V))
-    keys = sorted(recs, key=lambda k: (recs[k].features[0], k[:3]))
+        print(f"n={k[0]:6d} m~2^{k[2] / 4:.2f} " + " ".join(f"v{v}:{r.time_ms[v] * 1e3:8.1f}us/{r.error[v]:.0e}" for v in V))
+    keys = sorted(recs, key=lambda k: (recs[k].features[0], recs[k].features[1], k[:3]))
     train, held = keys[::2], keys[1::2]
     sel = tune.LearnedSelector(variants=V, device=dev, seed=0)
     hist = sel.fit([recs[k] for k in train], epochs=3000)
