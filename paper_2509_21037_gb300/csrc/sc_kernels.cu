@@ -140,11 +140,79 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const 
   }
 }
 
+// Diagonal output block (q1 == q2) of F = Y^T Y: only its lower triangle is
+// needed, and the FP64 pipe charges masked lanes in full, so the 528 lower
+// elements are dealt to the threads directly (slot u of thread t is element
+// t + 128 u, u < 5) and the chunk's tile is loaded once.
+__device__ __forceinline__ void syrk_diag_block(const PlanPtrs &P, const SyrkTask &t, const SubDev &sd,
+                                                const double *__restrict__ Y, double *__restrict__ F,
+                                                double (*As)[33]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jlo = t.q1 * kChunk;
+  constexpr int kLower = 32 * 33 / 2;   // 528
+  int rr[5], cc[5];
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    const int e = tid + kThreads * u;
+    int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;     // exact integer correction
+    while (r * (r + 1) / 2 > e) --r;
+    rr[u] = e < kLower ? r : 0;
+    cc[u] = e < kLower ? e - r * (r + 1) / 2 : 0;
+  }
+  const bool fifth = tid + kThreads * 4 < kLower;  // only the first 16 threads (warp 0) own slot 4
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int li = 0; li < t.list_len; ++li) {
+    const SnDev s = P.sns[P.syrk_list[t.list_off + li]];
+    const int ws = s.jhi - s.jlo;
+    const double *Ys = Y + s.y_off;
+    const int ja = jlo + lane - s.jlo;
+    const bool oka = ja >= 0 && ja < ws;
+    for (int k0 = 0; k0 < s.ns; k0 += 32) {
+      if (jlo >= P.cuts[s.cut_off + (k0 >> 5)]) continue;
+      const int kk = min(32, s.ns - k0);
+      for (int k = warp; k < kk; k += kThreads / 32) As[k][lane] = oka ? Ys[(int64_t)(k0 + k) * ws + ja] : 0.0;
+      __syncthreads();
+      if (warp == 0) {
+        for (int k = 0; k < kk; ++k) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = fma(As[k][rr[u]], As[k][cc[u]], acc[u]);
+          if (fifth) acc[4] = fma(As[k][rr[4]], As[k][cc[4]], acc[4]);
+        }
+      } else {
+        for (int k = 0; k < kk; ++k) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = fma(As[k][rr[u]], As[k][cc[u]], acc[u]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int32_t *perm = P.perm_cols + sd.col_off;
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    if (tid + kThreads * u >= kLower) continue;
+    const int j1 = jlo + rr[u], j2 = jlo + cc[u];
+    if (j1 < sd.m && j2 < sd.m) {
+      const int a = perm[j1], b = perm[j2];
+      const int hi = max(a, b), lo = min(a, b);
+      const int I = hi / kTile, J = lo / kTile;
+      double *T = F + sd.F_off + ((int64_t)I * (I + 1) / 2 + J) * (kTile * kTile);
+      T[(hi % kTile) + kTile * (lo % kTile)] = acc[u];
+      if (I == J) T[(lo % kTile) + kTile * (hi % kTile)] = acc[u];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) syrk_kernel(const PlanPtrs P, const double *__restrict__ Y,
                                                         double *__restrict__ F) {
   __shared__ double As[32][33], Bs[32][33];  // [k][column of the chunk]
   const SyrkTask t = P.syrk_tasks[blockIdx.x];
   const SubDev sd = P.subs[t.sub];
+  if (t.q1 == t.q2) {
+    syrk_diag_block(P, t, sd, Y, F, As);
+    return;
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j1lo = t.q1 * kChunk, j2lo = t.q2 * kChunk;
   double acc[8];
@@ -178,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) syrk_kernel(const PlanPtrs P, const 
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int j1 = j1lo + warp * 8 + u, j2 = j2lo + lane;
-    if (j1 < sd.m && j2 < sd.m && (t.q1 != t.q2 || j1 >= j2)) {
+    if (j1 < sd.m && j2 < sd.m) {
       const int a = perm[j1], b = perm[j2];
       const int hi = max(a, b), lo = min(a, b);
       const int I = hi / kTile, J = lo / kTile;

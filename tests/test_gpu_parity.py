@@ -312,3 +312,43 @@ def test_workspace_waves_match_single_wave(dev, split):
     plan.assemble(Lv, F)
     assert plan.device_status() == abi.SC_OK
     assert torch.equal(F, F_ref)
+
+
+def test_config5_full_size_sampled(dev):
+    """Config 5 (2048 subdomains: 2D heat k 32..96, 3D elasticity k 8..20)
+    assembled in one batch.  Sampled against the refined oracle: the smallest
+    and largest 2D squares and the smallest elasticity cube in full, the
+    largest elasticity cube (27783 dofs) on sampled columns.  Each is bounded
+    by 1e-12 over its FP64 input floor (the error of an exact solve with the
+    FP64-rounded factor; 2.6e-12 for the largest 2D square, fixed at one
+    corner node) and by 1e-12 against that exact solve."""
+    prob = synth.make_config(5)
+    fs = host.factorize_problem(prob.subdomains, threads=0)
+    plan, F, _ = _assemble(fs, prob.n_dual, dev)
+    n = np.array([f.n for f in fs])
+    is2d = np.array([s.ndpn == 1 for s in prob.subdomains])
+    memo = oracle._Memo()
+    full = [int(np.flatnonzero(is2d)[np.argmin(n[is2d])]), int(np.flatnonzero(is2d)[np.argmax(n[is2d])]),
+            int(np.flatnonzero(~is2d)[np.argmin(n[~is2d])])]
+    for i in full:
+        Fo = oracle.dual_operator(prob.subdomains[i], memo, refine=1)
+        Fg = plan.export(F, i).cpu().numpy()
+        FL = _exact_F_cols_given_L(fs[i], list(range(fs[i].m)))
+        floor = oracle.relative_frobenius(FL, Fo)
+        err = oracle.relative_frobenius(Fg, Fo)
+        print(f"subdomain {i} (n={fs[i].n}, m={fs[i].m}): err {err:.3e}, floor {floor:.3e}, "
+              f"kernel vs exact-with-L {oracle.relative_frobenius(Fg, FL):.3e}")
+        assert err <= floor + TOL
+        assert oracle.relative_frobenius(Fg, FL) <= TOL
+    big = int(np.flatnonzero(~is2d)[np.argmax(n[~is2d])])
+    sd = prob.subdomains[big]
+    cols = sorted(np.random.default_rng(1).choice(sd.m, size=12, replace=False).tolist())
+    Fo = oracle.dual_operator_columns(sd, cols, memo, refine=1)
+    Fg = plan.export(F, big).cpu().numpy()[:, cols]
+    FL = _exact_F_cols_given_L(fs[big], cols)
+    floor = oracle.relative_frobenius(FL, Fo)
+    err = oracle.relative_frobenius(Fg, Fo)
+    print(f"subdomain {big} (n={fs[big].n}, m={fs[big].m}): err {err:.3e}, floor {floor:.3e}, "
+          f"kernel vs exact-with-L {oracle.relative_frobenius(Fg, FL):.3e}")
+    assert err <= floor + TOL
+    assert oracle.relative_frobenius(Fg, FL) <= TOL
