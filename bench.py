@@ -181,6 +181,32 @@ def run_reference(args):
     return 0
 
 
+def _gpu_implicit(fs, n_dual, Lv, lam, q_expl, stream, reps=20):
+    """The GPU implicit application (include/sc_implicit.h) on the same L and
+    lambda: mean ms over `reps` calls, its FP64 roofline, and its relative
+    difference from the explicit q."""
+    import torch
+
+    from paper_2509_21037_gb300 import implicit
+    ip = implicit.ImplicitPlan(fs, n_dual).upload(lam.device)
+    q = torch.empty_like(lam)
+    ip.apply(Lv, lam, q, stream)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        ip.apply(Lv, lam, q, stream)
+    a1.record(stream)
+    a1.synchronize()
+    if ip.device_status(stream) != 0:
+        raise RuntimeError("device status not OK after the implicit apply")
+    ms = a0.elapsed_time(a1) / reps
+    tf = ip.sizes.flops / (ms / 1e3) / 1e12
+    diff = (torch.linalg.vector_norm(q - q_expl) / torch.linalg.vector_norm(q_expl)).item()
+    return ms, {"ms": ms, "flops": ip.sizes.flops, "nnz_visited": int(ip.sizes.nnz_visited),
+                "max_levels": int(ip.sizes.max_levels), "tflops": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS,
+                "rel_diff_vs_explicit": diff}
+
+
 def run_sc(args):
     import torch
     import torch.distributed as dist
@@ -250,6 +276,14 @@ def run_sc(args):
     value = world * nsub / (ms / 1e3)
 
     if args.profile:
+        if args.profile_implicit:
+            from paper_2509_21037_gb300 import implicit
+            ip = implicit.ImplicitPlan(fs, prob.n_dual).upload(dev)
+            for _ in range(args.warmup + args.steps):
+                ip.apply(Lv, lam, q, stream)
+            torch.cuda.synchronize(dev)
+            if ip.device_status(stream) != 0:
+                raise RuntimeError("device status not OK after the implicit apply")
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": ms, "stage_ms": {
                 "trsm": sum(trsm_ms) / len(trsm_ms), "syrk": sum(syrk_ms) / len(syrk_ms)}}))
@@ -296,6 +330,7 @@ def run_sc(args):
     a1.record(stream)
     a1.synchronize()
     t_expl = a0.elapsed_time(a1) / 20
+    t_gimpl, gimpl = _gpu_implicit(fs, prob.n_dual, Lv, lam, q, stream)
     impl = host.ImplicitApply(fs, prob.n_dual)
     lam_h = lam.cpu().numpy()
     impl(lam_h)
@@ -334,7 +369,10 @@ def run_sc(args):
                          "iterations_incl_L_h2d": (t_asm + (e2e_ms - ms)) / (t_impl - t_expl)
                          if t_impl > t_expl else None,
                          "t_assembly_ms": t_asm, "t_apply_explicit_gpu_ms": t_expl,
-                         "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count()},
+                         "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count(),
+                         "iterations_vs_gpu_implicit": t_asm / (t_gimpl - t_expl) if t_gimpl > t_expl else None,
+                         "t_apply_implicit_gpu_ms": t_gimpl},
+        "gpu_implicit_apply": gimpl,
         "gpu_launches": args.steps * 5,
         "clocks": clocks.summary(),
     }
@@ -475,6 +513,7 @@ def run_config5(args):
                "apply_GBps": plan.stats.bytes_apply / (sum(app) / len(app) / 1e3) / 1e9}
         F_off = plan.F_offsets.copy()
         st = plan.stats_dict()
+        out["q"] = q
         del plan
         torch.cuda.empty_cache()
         return out, (F if keep_F else None), F_off, st
@@ -488,6 +527,11 @@ def run_config5(args):
         nr = torch.linalg.vector_norm(F64[a:b]).item()
         errs.append(torch.linalg.vector_norm(Fsel[a:b] - F64[a:b]).item() / max(nr, 1e-300))
     del Fsel
+    q_expl = r64.pop("q")
+    rsel.pop("q")
+    del F64
+    torch.cuda.empty_cache()
+    t_gimpl, gimpl = _gpu_implicit(fs, prob.n_dual, Lv, lam, q_expl, None, reps=3)
     impl = host.ImplicitApply(fs, prob.n_dual)
     lam_h = lam.cpu().numpy()
     impl(lam_h)
@@ -511,7 +555,11 @@ def run_config5(args):
         "effective_tflops_selected": st["flops_dense"] / (rsel["assembly_ms"] / 1e3) / 1e12,
         "amortization": {"iterations": rsel["assembly_ms"] / (t_impl - rsel["apply_ms"]),
                          "iterations_fp64_only": r64["assembly_ms"] / (t_impl - r64["apply_ms"]),
-                         "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count()},
+                         "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count(),
+                         "iterations_vs_gpu_implicit": rsel["assembly_ms"] / (t_gimpl - rsel["apply_ms"])
+                         if t_gimpl > rsel["apply_ms"] else None,
+                         "t_apply_implicit_gpu_ms": t_gimpl},
+        "gpu_implicit_apply": gimpl,
         "autotune": {"classes_measured": len(recs), "classes_total": len(keys), "seconds": t_tune},
         "host_factorisation_s": t_prep,
     }
@@ -539,6 +587,8 @@ def main():
     ap.add_argument("--ws-limit-gb", type=float, default=48.0, help="config 5: workspace bound per wave")
     ap.add_argument("--profile-slices", type=int, default=0,
                     help="with --profile: run the split-precision variant with this many slices")
+    ap.add_argument("--profile-implicit", action="store_true",
+                    help="with --profile: also run the GPU implicit apply warmup + steps times")
     ap.add_argument("--profile", action="store_true",
                     help="device steps only (no e2e, comparator or CPU baseline): for ncu captures")
     args = ap.parse_args()

@@ -56,7 +56,8 @@ def _run_parallel(cmds: List[List[str]]) -> None:
 def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
     os.makedirs(OBJ, exist_ok=True)
     cuda = _cuda_home()
-    cu_main = ["sc_plan.cpp", "sc_api.cu", "sc_kernels.cu", "sc_static.cu", "sc_split.cu", "sc_mlp.cu"]
+    cu_main = ["sc_plan.cpp", "sc_api.cu", "sc_kernels.cu", "sc_static.cu", "sc_split.cu", "sc_mlp.cu",
+               "sc_implicit.cu"]
     objs_main = []
     cmds = []
     for s in cu_main:

@@ -1,4 +1,4 @@
-"""ctypes mirror of include/sc.h and include/sc_dense.h (argument marshalling only)."""
+"""ctypes mirror of include/sc.h, include/sc_implicit.h and include/sc_dense.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -62,6 +62,29 @@ SC_SYMBOLS = {
     "sc_destroy": ([c_vp], None),
 }
 
+class ImplicitSizes(ctypes.Structure):
+    _fields_ = [("plan_bytes", c_sz), ("ws_bytes", c_sz), ("L_values", c_i64), ("n_supernodes", c_i64),
+                ("nnz_visited", c_i64), ("max_levels", c_i64), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("n_cluster_subdomains", c_i64)]
+
+
+class ImplicitOptions(ctypes.Structure):
+    _fields_ = [("cluster_min_work", c_i64), ("reserved", c_i32 * 2)]
+
+
+# every symbol include/sc_implicit.h declares
+IMPLICIT_SYMBOLS = {
+    "sci_plan": ([ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(SubdomainDesc), c_i64,
+                  ctypes.POINTER(ImplicitOptions)], c_int),
+    "sci_get_sizes": ([c_vp, ctypes.POINTER(ImplicitSizes)], c_int),
+    "sci_upload_plan": ([c_vp, c_vp, c_sz, c_vp], c_int),
+    "sci_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp], c_int),
+    "sci_device_status": ([c_vp, c_vp, c_vp], c_int),
+    "sci_export_plan": ([c_vp, c_vp, c_sz], c_int),
+    "sci_last_error": ([c_vp], ctypes.c_char_p),
+    "sci_destroy": ([c_vp], None),
+}
+
 DENSE_SYMBOLS = {
     "scd_create": ([ctypes.POINTER(c_vp), c_i32], c_int),
     "scd_trsm_syrk": ([c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
@@ -78,6 +101,7 @@ def _declare(lib, table):
 
 def declare(lib):
     _declare(lib, SC_SYMBOLS)
+    _declare(lib, IMPLICIT_SYMBOLS)
 
 
 def declare_dense(lib):

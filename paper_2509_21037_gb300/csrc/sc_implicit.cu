@@ -1,0 +1,718 @@
+// Implicit application of the dual operator on the GPU (include/sc_implicit.h):
+// per subdomain q += B L^{-T} L^{-1} B^T lambda with two sparse triangular
+// solves over the supernodes of L (paper Sec. 2.2, Eq. "dualop_apply_impl").
+//
+// Host side (sci_plan): the symbolic analysis of sc_plan (fundamental
+// supernodes, the supernodes reached from B^T's rows), then per subdomain a
+// level schedule of the reached supernodes by etree height (leaves 0; a
+// parent is at least one level above each child), B^T grouped by row for the
+// gather and by entry for the scatter.
+//
+// Device side: one CTA per subdomain (largest first).  Forward solve level by
+// level upwards, backward solve level by level downwards, the warps sharing
+// the supernodes of a level; a barrier between levels.  A warp solves its
+// supernode in 32-column blocks:
+//   forward   the block's triangle with lane = row (32 shuffle steps, the
+//             block's L entries prefetched into registers), then the panel
+//             below (the supernode's remaining diagonal rows and its pruned
+//             rows) updated with lane = row and coalesced column reads;
+//             updates of ancestor rows are FP64 atomic additions (other
+//             warps of the level may hit the same ancestor row);
+//   backward  blocks in descending order; the panel's contribution
+//             sum_t L(t, k) z_t per block column k accumulated per lane
+//             (lane = row, coalesced column reads) and summed across the warp
+//             by a 31-step transpose-reduce (lane k ends with column k), then
+//             the transposed triangle with lane = column.
+// Levels with fewer than four supernodes (the top of the tree, where the
+// large separators are) run each supernode on the whole CTA instead: warp 0
+// solves the triangle, all warps share the panel rows.
+// A fundamental supernode's CSC columns are its dense trapezoidal panel
+// columns: local column t (0-based) holds rows t..ns-1 of the diagonal block
+// then the rs pruned rows, and starts off(t) = t (ns + rs) - t (t - 1) / 2
+// entries after column 0's diagonal.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sc_implicit.h"
+#include "sc_internal.h"
+
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int kWarps = 8;
+constexpr int kCluster = 8;     // CTAs per cluster (portable maximum)
+constexpr int64_t kCtaSlots = 152 * 2;   // resident CTAs on a GB300 (152 SMs, 2 CTAs each)
+constexpr int kThreadsI = 32 * kWarps;
+constexpr uint32_t kFull = 0xffffffffu;
+
+struct ISub {
+  int64_t x_off;                // doubles, this subdomain's n-vector in the workspace
+  int32_t n, sn_lo, sn_hi;      // supernodes [sn_lo, sn_hi), ordered by (level, first column)
+  int32_t lev_lo, n_lev;        // level boundaries levptr[lev_lo .. lev_lo + n_lev]
+  int32_t g_lo, g_hi;           // gather rows
+  int32_t s_lo, s_hi;           // scatter entries
+  int32_t pad;
+};
+static_assert(sizeof(ISub) == 48, "ISub layout");
+
+struct ISn {
+  int64_t lval;      // absolute index of L(c0, c0) in the concatenated values
+  int64_t rows_off;  // first of the rs pruned rows in `rows`
+  int32_t c0, ns, rs, sub;
+};
+static_assert(sizeof(ISn) == 32, "ISn layout");
+
+struct IRow {
+  int32_t r, e_lo, e_hi, pad;   // local row r of B^T, its entries [e_lo, e_hi) in gent
+};
+struct IEnt {
+  int32_t gj, sign;             // global multiplier, +1 / -1
+};
+struct ISEnt {
+  int32_t r, gj, sign, pad;     // one B^T entry: local row, global multiplier, sign
+};
+
+struct IItem {
+  int32_t kind;                 // 0: sub[0] on the whole cluster; 1: sub[r] on CTA r, r < n
+  int32_t n;
+  int32_t sub[kCluster];        // indices into the subdomain table
+};
+static_assert(sizeof(IItem) == 40, "IItem layout");
+
+constexpr int kSections = 8;
+struct IHeader {
+  uint32_t magic;     // 'SCIP'
+  uint32_t version;   // 1
+  int32_t nsub, pad;
+  int64_t n_sn, n_levptr, n_rows, n_grow, n_gent, n_sent, n_items;
+  uint64_t sec_off[kSections];   // subs sns levptr rows grow gent sent items
+};
+constexpr size_t kIHeaderBytes = 256;
+static_assert(sizeof(IHeader) <= kIHeaderBytes, "implicit plan header");
+
+struct IPtrs {
+  const ISub *subs;
+  const ISn *sns;
+  const int32_t *levptr;
+  const int32_t *rows;
+  const IRow *grow;
+  const IEnt *gent;
+  const ISEnt *sent;
+  const IItem *items;
+};
+
+__device__ __forceinline__ int64_t col_off(int t, int nr) {
+  return (int64_t)t * nr - (int64_t)t * (t - 1) / 2;
+}
+
+// Loads of x: when a subdomain spans a cluster, x is written by several SMs
+// and read after cluster barriers, so reads bypass the (non-coherent) L1.
+template <bool CL>
+__device__ __forceinline__ double ldx(const double *p) {
+  if constexpr (CL) return __ldcg(p);
+  else return *p;
+}
+
+// Forward triangle of one 32-column block (one warp, lane = row): y = L_bb^{-1} x_b,
+// written to x; returns the lane's y (0 for lanes >= w).
+template <bool CL>
+__device__ __forceinline__ double forward_triangle(const double *__restrict__ L, int nr, int kb, int w, double *xs,
+                                                   uint32_t *status, int lane) {
+  const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
+  double inv = 0.0;
+  if (lane < w) {
+    const double d = L[coff];
+    if (d > 0.0 && d <= 1.79769313486231570e308) inv = 1.0 / d;
+    else atomicOr(status, 1u);
+  }
+  // lane i: L(kb + i, kb + k) for k < i, entry (i - k) of column kb + k
+  double lv[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    lv[k] = 0.0;
+    if (k < w) {
+      const int64_t ck = __shfl_sync(kFull, coff, k);
+      if (k < lane && lane < w) lv[k] = L[ck + (lane - k)];
+    }
+  }
+  double xi = lane < w ? ldx<CL>(xs + kb + lane) : 0.0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < w) {   // uniform
+      const double yk = __shfl_sync(kFull, xi, k) * __shfl_sync(kFull, inv, k);
+      xi = lane == k ? yk : fma(-lv[k], yk, xi);
+    }
+  }
+  if (lane < w) xs[kb + lane] = xi;
+  return xi;
+}
+
+// Forward panel update for local rows t0 + lane (one warp):
+// x_t -= sum_k L(t, kb + k) y_k.  Rows of the supernode's own diagonal block
+// belong to this warp alone; rows below are ancestors' rows that other warps
+// (or SMs) may update at the same level: atomic.
+template <bool CL>
+__device__ __forceinline__ void forward_panel_chunk(const double *__restrict__ L, const int32_t *__restrict__ R,
+                                                    int ns, int nr, int kb, int w, int t0, const double *ys,
+                                                    double *xs, double *x, int lane) {
+  const int t = t0 + lane;
+  const bool ok = t < nr;
+  double lv[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) lv[k] = (k < w && ok) ? L[col_off(kb + k, nr) + (t - kb - k)] : 0.0;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    if (k < w) acc = fma(lv[k], ys[k], acc);
+  if (!ok) return;
+  if (t < ns) xs[t] = ldx<CL>(xs + t) - acc;
+  else atomicAdd(x + R[t - ns], -acc);
+}
+
+// Backward: per-lane partial sums acc[k] += L(t, kb + k) z_t over local rows t0 + lane.
+template <bool CL>
+__device__ __forceinline__ void backward_panel_chunk(const double *__restrict__ L, const int32_t *__restrict__ R,
+                                                     int ns, int nr, int kb, int w, int t0, const double *xs,
+                                                     const double *x, double (&acc)[32], int lane) {
+  const int t = t0 + lane;
+  const bool ok = t < nr;
+  const double zt = ok ? (t < ns ? ldx<CL>(xs + t) : ldx<CL>(x + R[t - ns])) : 0.0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    if (k < w && ok) acc[k] = fma(L[col_off(kb + k, nr) + (t - kb - k)], zt, acc[k]);
+}
+
+// Warp transpose-reduce: on return lane k holds the sum over the warp's lanes
+// of acc[k] (31 shuffle-add steps; acc is destroyed).
+__device__ __forceinline__ double transpose_reduce(double (&acc)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const double send = up ? acc[j] : acc[j + h];
+      const double keep = up ? acc[j + h] : acc[j];
+      acc[j] = keep + __shfl_xor_sync(kFull, send, h);
+    }
+  }
+  return acc[0];
+}
+
+// Backward triangle of one block (one warp, lane = column): z = L_bb^{-T} rhs, written to x.
+__device__ __forceinline__ void backward_triangle(const double *__restrict__ L, int nr, int kb, int w, double rhs,
+                                                  double *xs, int lane) {
+  const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
+  const double inv = lane < w ? 1.0 / L[coff] : 0.0;
+  // lane k: L(kb + i, kb + k) for i > k, entry (i - k) of its own column
+  double lc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) lc[i] = (i > lane && i < w) ? L[coff + (i - lane)] : 0.0;
+#pragma unroll
+  for (int i = 31; i >= 0; --i) {
+    if (i < w) {   // uniform
+      if (lane == i) rhs *= inv;
+      const double zi = __shfl_sync(kFull, rhs, i);
+      rhs = fma(-lc[i], zi, rhs);
+    }
+  }
+  if (lane < w) xs[kb + lane] = rhs;
+}
+
+// A group of warps solving supernodes together: the whole cluster, or one
+// CTA.  Warps are numbered across the group.
+struct Group {
+  int rank, size, warp, lane, gw, nw;
+  bool cluster;
+  __device__ void sync() const {
+    if (cluster) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+};
+
+__device__ __forceinline__ Group cta_group(int warp, int lane) {
+  return Group{0, 1, warp, lane, warp, kWarps, false};
+}
+
+__device__ __forceinline__ Group cluster_group(int warp, int lane) {
+  cg::cluster_group c = cg::this_cluster();
+  const int r = (int)c.block_rank(), n = (int)c.num_blocks();
+  return Group{r, n, warp, lane, r * kWarps + warp, n * kWarps, true};
+}
+
+// One supernode by one warp.
+template <bool CL>
+__device__ void forward_warp(const ISn &sn, const double *__restrict__ Lv, const int32_t *__restrict__ rows,
+                             double *x, double *ys, uint32_t *status, int lane) {
+  const int ns = sn.ns, nr = ns + sn.rs;
+  const double *L = Lv + sn.lval;
+  const int32_t *R = rows + sn.rows_off;
+  double *xs = x + sn.c0;
+  for (int kb = 0; kb < ns; kb += 32) {
+    const int w = min(32, ns - kb);
+    ys[lane] = forward_triangle<CL>(L, nr, kb, w, xs, status, lane);
+    __syncwarp();
+    for (int t0 = kb + w; t0 < nr; t0 += 32) forward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, ys, xs, x, lane);
+    __syncwarp();
+  }
+}
+
+template <bool CL>
+__device__ void backward_warp(const ISn &sn, const double *__restrict__ Lv, const int32_t *__restrict__ rows,
+                              double *x, int lane) {
+  const int ns = sn.ns, nr = ns + sn.rs;
+  const double *L = Lv + sn.lval;
+  const int32_t *R = rows + sn.rows_off;
+  double *xs = x + sn.c0;
+  for (int kb = ((ns - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int w = min(32, ns - kb);
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int t0 = kb + w; t0 < nr; t0 += 32) backward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, xs, x, acc, lane);
+    const double part = transpose_reduce(acc, lane);
+    const double rhs = lane < w ? ldx<CL>(xs + kb + lane) - part : 0.0;
+    backward_triangle(L, nr, kb, w, rhs, xs, lane);
+    __syncwarp();
+  }
+}
+
+// One supernode by a CTA (CL = false; warps of this CTA) or by the whole
+// cluster (CL = true): the triangle by the group's first warp, the panel rows
+// spread over all the group's warps.
+template <bool CL>
+__device__ void forward_group(const Group &g, const ISn &sn, const double *__restrict__ Lv,
+                              const int32_t *__restrict__ rows, double *x, double *ys, uint32_t *status) {
+  const int ns = sn.ns, nr = ns + sn.rs;
+  const double *L = Lv + sn.lval;
+  const int32_t *R = rows + sn.rows_off;
+  double *xs = x + sn.c0;
+  for (int kb = 0; kb < ns; kb += 32) {
+    const int w = min(32, ns - kb);
+    if (g.gw == 0) forward_triangle<CL>(L, nr, kb, w, xs, status, g.lane);
+    g.sync();
+    ys[g.lane] = g.lane < w ? ldx<CL>(xs + kb + g.lane) : 0.0;
+    __syncwarp();
+    for (int t0 = kb + w + 32 * g.gw; t0 < nr; t0 += 32 * g.nw)
+      forward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, ys, xs, x, g.lane);
+    g.sync();
+  }
+}
+
+// red: this CTA's kWarps x 32 doubles; red_cta: its 32-double sum (read by
+// the group's first CTA through distributed shared memory when CL).
+template <bool CL>
+__device__ void backward_group(const Group &g, const ISn &sn, const double *__restrict__ Lv,
+                               const int32_t *__restrict__ rows, double *x, double *red, double *red_cta) {
+  const int ns = sn.ns, nr = ns + sn.rs;
+  const double *L = Lv + sn.lval;
+  const int32_t *R = rows + sn.rows_off;
+  double *xs = x + sn.c0;
+  for (int kb = ((ns - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int w = min(32, ns - kb);
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int t0 = kb + w + 32 * g.gw; t0 < nr; t0 += 32 * g.nw)
+      backward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, xs, x, acc, g.lane);
+    red[g.warp * 32 + g.lane] = transpose_reduce(acc, g.lane);
+    __syncthreads();
+    if (g.warp == 0) {
+      double s = 0.0;
+#pragma unroll
+      for (int v = 0; v < kWarps; ++v) s += red[v * 32 + g.lane];
+      red_cta[g.lane] = s;
+    }
+    g.sync();
+    if (g.gw == 0) {
+      double part = red_cta[g.lane];
+      if (g.cluster) {
+        cg::cluster_group c = cg::this_cluster();
+        for (int r = 1; r < g.size; ++r) part += c.map_shared_rank(red_cta, r)[g.lane];
+      }
+      const double rhs = g.lane < w ? ldx<CL>(xs + kb + g.lane) - part : 0.0;
+      backward_triangle(L, nr, kb, w, rhs, xs, g.lane);
+    }
+    g.sync();
+  }
+}
+
+// The whole implicit application for one subdomain by one group (CL: the
+// cluster; x is then read past L1).  Per etree level, by its supernode count
+// c: c >= half the group's warps -- one warp per supernode; else c >= the
+// group's CTAs -- one CTA per supernode (the CTA's warps share its panel
+// rows); else (the top separators) one supernode at a time on the whole
+// group.  One group barrier per level, two per 32-column block in the last case.
+template <bool CL>
+__device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, const double *__restrict__ Lv,
+                                const double *__restrict__ lam, double *q, double *X, uint32_t *status,
+                                double (*ys)[32], double *red, double *red_cta) {
+  const int tid = g.warp * 32 + g.lane;
+  const int gt = g.rank * kThreadsI + tid, nt = g.size * kThreadsI;
+  const Group cta = cta_group(g.warp, g.lane);
+  double *x = X + sd.x_off;
+  // x = 0, then x = B^T lambda
+  for (int c = gt; c < sd.n; c += nt) x[c] = 0.0;
+  g.sync();
+  for (int r = sd.g_lo + gt; r < sd.g_hi; r += nt) {
+    const IRow row = P.grow[r];
+    double v = 0.0;
+    for (int e = row.e_lo; e < row.e_hi; ++e) v += P.gent[e].sign * lam[P.gent[e].gj];
+    x[row.r] = v;
+  }
+  g.sync();
+  for (int l = 0; l < sd.n_lev; ++l) {
+    const int a = P.levptr[sd.lev_lo + l], b = P.levptr[sd.lev_lo + l + 1];
+    if (2 * (b - a) >= g.nw) {
+      for (int s = a + g.gw; s < b; s += g.nw) forward_warp<CL>(P.sns[s], Lv, P.rows, x, ys[g.warp], status, g.lane);
+      g.sync();
+    } else if (b - a >= g.size) {
+      for (int s = a + g.rank; s < b; s += g.size) forward_group<CL>(cta, P.sns[s], Lv, P.rows, x, ys[g.warp], status);
+      if (g.cluster) g.sync();
+    } else {
+      for (int s = a; s < b; ++s) forward_group<CL>(g, P.sns[s], Lv, P.rows, x, ys[g.warp], status);
+    }
+  }
+  for (int l = sd.n_lev - 1; l >= 0; --l) {
+    const int a = P.levptr[sd.lev_lo + l], b = P.levptr[sd.lev_lo + l + 1];
+    if (2 * (b - a) >= g.nw) {
+      for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, g.lane);
+      g.sync();
+    } else if (b - a >= g.size) {
+      for (int s = a + g.rank; s < b; s += g.size) backward_group<CL>(cta, P.sns[s], Lv, P.rows, x, red, red_cta);
+      if (g.cluster) g.sync();
+    } else {
+      for (int s = a; s < b; ++s) backward_group<CL>(g, P.sns[s], Lv, P.rows, x, red, red_cta);
+    }
+  }
+  for (int e = sd.s_lo + gt; e < sd.s_hi; e += nt) {
+    const ISEnt t = P.sent[e];
+    atomicAdd(q + t.gj, t.sign * ldx<CL>(x + t.r));
+  }
+}
+
+// Launched in clusters of kCluster CTAs.  An item is either one large
+// subdomain solved by the whole cluster, or up to kCluster small subdomains,
+// one per CTA.
+__global__ void __launch_bounds__(kThreadsI, 2) implicit_kernel(const IPtrs P, const double *__restrict__ Lv,
+                                                                const double *__restrict__ lam, double *q,
+                                                                double *X, uint32_t *status) {
+  __shared__ double ys[kWarps][32];
+  __shared__ double red[kWarps * 32];
+  __shared__ double red_cta[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const IItem it = P.items[blockIdx.x / kCluster];
+  if (it.kind == 0) {
+    const Group g = cluster_group(warp, lane);
+    solve_subdomain<true>(g, P, P.subs[it.sub[0]], Lv, lam, q, X, status, ys, red, red_cta);
+    cg::this_cluster().sync();   // no CTA leaves while the first one may read its shared memory
+  } else {
+    const int r = (int)(blockIdx.x % kCluster);   // also without a cluster launch
+    if (r < it.n) {
+      const Group g = cta_group(warp, lane);
+      solve_subdomain<false>(g, P, P.subs[it.sub[r]], Lv, lam, q, X, status, ys, red, red_cta);
+    }
+  }
+}
+
+}  // namespace
+
+struct sci_ctx {
+  std::string err;
+  int32_t nsub = 0;
+  int64_t n_dual = 0;
+  std::vector<uint8_t> blob;
+  IHeader hdr{};
+  sci_sizes sizes{};
+  void *plan_dev = nullptr;
+  size_t plan_dev_bytes = 0;
+  int64_t n_items = 0;
+
+  IPtrs ptrs() const {
+    const uint8_t *b = static_cast<const uint8_t *>(plan_dev);
+    IPtrs p;
+    p.subs = reinterpret_cast<const ISub *>(b + hdr.sec_off[0]);
+    p.sns = reinterpret_cast<const ISn *>(b + hdr.sec_off[1]);
+    p.levptr = reinterpret_cast<const int32_t *>(b + hdr.sec_off[2]);
+    p.rows = reinterpret_cast<const int32_t *>(b + hdr.sec_off[3]);
+    p.grow = reinterpret_cast<const IRow *>(b + hdr.sec_off[4]);
+    p.gent = reinterpret_cast<const IEnt *>(b + hdr.sec_off[5]);
+    p.sent = reinterpret_cast<const ISEnt *>(b + hdr.sec_off[6]);
+    p.items = reinterpret_cast<const IItem *>(b + hdr.sec_off[7]);
+    return p;
+  }
+};
+
+namespace {
+
+template <class V>
+size_t put_section(std::vector<uint8_t> &blob, const std::vector<V> &v) {
+  const size_t off = (blob.size() + 255) & ~size_t(255);
+  blob.resize(off + v.size() * sizeof(V));
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(V));
+  return off;
+}
+
+sc_status ifail(sci_ctx *c, sc_status st, const std::string &m) {
+  if (c) c->err = m;
+  return st;
+}
+
+sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t cluster_min_work) {
+  std::vector<ISub> subs;
+  std::vector<ISn> sns;
+  std::vector<int32_t> levptr, rows;
+  std::vector<IRow> grow;
+  std::vector<IEnt> gent;
+  std::vector<ISEnt> sent;
+  // subdomains largest first (CTA order), by visited entries of L
+  std::vector<sc::SubPlan> P(nsub);
+  std::vector<int64_t> work(nsub, 0), L_off(nsub + 1, 0), x_off(nsub + 1, 0);
+  int64_t max_lev = 0, nnz_all = 0, m_all = 0;
+  for (int32_t i = 0; i < nsub; ++i) {
+    const std::string e = sc::analyze(i, d[i], P[i]);
+    if (!e.empty()) return ifail(ctx, SC_ERR_INVALID_ARG, e);
+    if (d[i].m > 0 && !d[i].lambda_map)
+      return ifail(ctx, SC_ERR_INVALID_ARG, "subdomain " + std::to_string(i) + ": lambda_map is NULL");
+    for (int32_t j = 0; j < d[i].m; ++j)
+      if (d[i].lambda_map[j] < 0 || d[i].lambda_map[j] >= ctx->n_dual)
+        return ifail(ctx, SC_ERR_INVALID_ARG, "subdomain " + std::to_string(i) + ": lambda_map out of range");
+    L_off[i + 1] = L_off[i] + (d[i].n > 0 ? d[i].L_colptr[d[i].n] : 0);
+    x_off[i + 1] = x_off[i] + d[i].n;
+    const sc::SubPlan &S = P[i];
+    for (size_t s = 0; s < S.sn_c0.size(); ++s)
+      if (S.sn_jhi[s] > S.sn_jlo[s])
+        work[i] += (int64_t)S.sn_ns[s] * (S.sn_ns[s] + 1) / 2 + (int64_t)S.sn_ns[s] * S.sn_rs[s];
+    nnz_all += work[i];
+    m_all += d[i].m;
+  }
+  std::vector<int32_t> order(nsub);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+  for (int32_t i : order) {
+    const sc::SubPlan &S = P[i];
+    const sc_subdomain_desc &D = d[i];
+    const int32_t nsn = (int32_t)S.sn_c0.size();
+    std::vector<int32_t> h(nsn, 0), vis;
+    for (int32_t s = 0; s < nsn; ++s) {
+      if (S.sn_jhi[s] <= S.sn_jlo[s]) continue;
+      vis.push_back(s);
+      if (S.sparent[s] >= 0) h[S.sparent[s]] = std::max(h[S.sparent[s]], h[s] + 1);
+    }
+    std::stable_sort(vis.begin(), vis.end(), [&](int32_t a, int32_t b) { return h[a] < h[b]; });
+    ISub sd{};
+    sd.x_off = x_off[i];
+    sd.n = D.n;
+    sd.sn_lo = (int32_t)sns.size();
+    sd.lev_lo = (int32_t)levptr.size();
+    int32_t cur = -1;
+    for (int32_t s : vis) {
+      while (cur < h[s]) {
+        levptr.push_back((int32_t)sns.size());
+        ++cur;
+      }
+      ISn sn{};
+      const int32_t c0 = S.sn_c0[s], ns = S.sn_ns[s], rs = S.sn_rs[s];
+      sn.lval = L_off[i] + D.L_colptr[c0];
+      sn.rows_off = (int64_t)rows.size();
+      sn.c0 = c0;
+      sn.ns = ns;
+      sn.rs = rs;
+      sn.sub = i;
+      const int64_t last = D.L_colptr[c0 + ns - 1];
+      for (int32_t k = 0; k < rs; ++k) rows.push_back(D.L_rowind[last + 1 + k]);
+      sns.push_back(sn);
+    }
+    sd.sn_hi = (int32_t)sns.size();
+    sd.n_lev = cur + 1;
+    levptr.push_back(sd.sn_hi);
+    max_lev = std::max<int64_t>(max_lev, sd.n_lev);
+    // B^T by row (gather) and by entry (scatter)
+    std::vector<std::pair<int32_t, int32_t>> ent;   // (row, entry index)
+    for (int32_t j = 0; j < D.m; ++j)
+      for (int32_t e = D.Bt_colptr[j]; e < D.Bt_colptr[j + 1]; ++e) {
+        ent.emplace_back(D.Bt_rowind[e], e);
+        sent.push_back(ISEnt{D.Bt_rowind[e], D.lambda_map[j], (int32_t)D.Bt_sign[e], 0});
+      }
+    std::vector<int32_t> col_of(ent.size());
+    for (int32_t j = 0; j < D.m; ++j)
+      for (int32_t e = D.Bt_colptr[j]; e < D.Bt_colptr[j + 1]; ++e) col_of[e] = j;
+    std::stable_sort(ent.begin(), ent.end());
+    sd.g_lo = (int32_t)grow.size();
+    for (size_t a = 0; a < ent.size();) {
+      size_t b = a;
+      IRow r{ent[a].first, (int32_t)gent.size(), 0, 0};
+      while (b < ent.size() && ent[b].first == ent[a].first) {
+        const int32_t e = ent[b].second;
+        gent.push_back(IEnt{D.lambda_map[col_of[e]], (int32_t)D.Bt_sign[e]});
+        ++b;
+      }
+      r.e_hi = (int32_t)gent.size();
+      grow.push_back(r);
+      a = b;
+    }
+    sd.g_hi = (int32_t)grow.size();
+    sd.s_hi = (int32_t)sent.size();
+    sd.s_lo = sd.s_hi - (int32_t)ent.size();
+    subs.push_back(sd);
+  }
+  // items: subdomains with at least cluster_min_work visited entries get a
+  // cluster each; the rest are packed kCluster to a cluster, one per CTA
+  // (subs is largest first, so packed neighbours have similar work)
+  // automatic: a cluster for a subdomain with more than twice an even share
+  // of the CTAs the batch can occupy (measured on GB300: clusters shorten a
+  // heavy tail of a few large subdomains, but cost more than they give on a
+  // batch of similar ones)
+  if (cluster_min_work < 0)
+    cluster_min_work = std::max<int64_t>(1, 2 * nnz_all / std::max<int64_t>(1, std::min<int64_t>(kCtaSlots, nsub)) + 1);
+  std::vector<IItem> items;
+  for (int32_t k = 0; k < nsub;) {
+    IItem it{};
+    if (work[order[k]] >= cluster_min_work) {
+      it.kind = 0;
+      it.n = 1;
+      it.sub[0] = k++;
+    } else {
+      it.kind = 1;
+      while (it.n < kCluster && k < nsub) it.sub[it.n++] = k++;
+    }
+    items.push_back(it);
+  }
+  ctx->n_items = (int64_t)items.size();
+  int64_t n_big = 0;
+  for (const IItem &it : items) n_big += it.kind == 0;
+  IHeader &H = ctx->hdr;
+  H = IHeader{};
+  H.magic = 0x50494353u;   // "SCIP"
+  H.version = 1;
+  H.nsub = nsub;
+  H.n_sn = (int64_t)sns.size();
+  H.n_levptr = (int64_t)levptr.size();
+  H.n_rows = (int64_t)rows.size();
+  H.n_grow = (int64_t)grow.size();
+  H.n_gent = (int64_t)gent.size();
+  H.n_sent = (int64_t)sent.size();
+  H.n_items = (int64_t)items.size();
+  std::vector<uint8_t> &blob = ctx->blob;
+  blob.assign(kIHeaderBytes, 0);
+  H.sec_off[0] = put_section(blob, subs);
+  H.sec_off[1] = put_section(blob, sns);
+  H.sec_off[2] = put_section(blob, levptr);
+  H.sec_off[3] = put_section(blob, rows);
+  H.sec_off[4] = put_section(blob, grow);
+  H.sec_off[5] = put_section(blob, gent);
+  H.sec_off[6] = put_section(blob, sent);
+  H.sec_off[7] = put_section(blob, items);
+  blob.resize((blob.size() + 255) & ~size_t(255));
+  std::memcpy(blob.data(), &H, sizeof(H));
+  sci_sizes &z = ctx->sizes;
+  z.plan_bytes = blob.size();
+  z.ws_bytes = 256 + sizeof(double) * (size_t)x_off[nsub];
+  z.L_values = L_off[nsub];
+  z.n_supernodes = (int64_t)sns.size();
+  z.nnz_visited = nnz_all;
+  z.max_levels = max_lev;
+  z.flops = 4.0 * (double)nnz_all;
+  z.n_cluster_subdomains = n_big;
+  z.bytes = 16.0 * (double)nnz_all + 16.0 * (double)m_all;
+  return SC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sci_plan(sci_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomains, int64_t n_dual,
+                   const sci_options *opt) {
+  if (!out) return SC_ERR_INVALID_ARG;
+  *out = nullptr;
+  sci_ctx *ctx = new sci_ctx();
+  *out = ctx;
+  if (nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0)
+    return ifail(ctx, SC_ERR_INVALID_ARG, "nsub < 0, n_dual < 0 or subdomains NULL");
+  ctx->nsub = nsub;
+  ctx->n_dual = n_dual;
+  return build(ctx, nsub, subdomains, opt ? opt->cluster_min_work : -1);
+}
+
+sc_status sci_get_sizes(const sci_ctx *ctx, sci_sizes *s) {
+  if (!ctx || !s) return SC_ERR_INVALID_ARG;
+  *s = ctx->sizes;
+  return SC_OK;
+}
+
+sc_status sci_upload_plan(sci_ctx *ctx, void *plan_dev, size_t bytes, void *stream) {
+  if (!ctx) return SC_ERR_INVALID_ARG;
+  if (!plan_dev || bytes < ctx->blob.size()) return ifail(ctx, SC_ERR_INVALID_ARG, "plan buffer NULL or too small");
+  if (reinterpret_cast<uintptr_t>(plan_dev) % 256) return ifail(ctx, SC_ERR_INVALID_ARG, "plan buffer not 256-byte aligned");
+  cudaError_t e = cudaMemcpyAsync(plan_dev, ctx->blob.data(), ctx->blob.size(), cudaMemcpyHostToDevice,
+                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return ifail(ctx, SC_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  // the host blob must stay alive until the asynchronous copy has read it
+  const cudaError_t e2 = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e2 != cudaSuccess) return ifail(ctx, SC_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e2));
+  ctx->plan_dev = plan_dev;
+  ctx->plan_dev_bytes = bytes;
+  return SC_OK;
+}
+
+sc_status sci_apply(sci_ctx *ctx, const double *L_values_dev, const double *lambda_dev, double *q_dev, void *ws_dev,
+                    size_t ws_bytes, void *stream) {
+  if (!ctx) return SC_ERR_INVALID_ARG;
+  if (!ctx->plan_dev) return ifail(ctx, SC_ERR_STATE, "sci_upload_plan was not called");
+  if (ctx->n_dual > 0 && (!lambda_dev || !q_dev)) return ifail(ctx, SC_ERR_INVALID_ARG, "lambda or q is NULL");
+  if (ctx->sizes.L_values > 0 && !L_values_dev) return ifail(ctx, SC_ERR_INVALID_ARG, "L_values_dev is NULL");
+  if (!ws_dev || ws_bytes < ctx->sizes.ws_bytes) return ifail(ctx, SC_ERR_OOM, "workspace NULL or too small");
+  if (reinterpret_cast<uintptr_t>(ws_dev) % 256) return ifail(ctx, SC_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t *status = static_cast<uint32_t *>(ws_dev);
+  double *X = reinterpret_cast<double *>(static_cast<uint8_t *>(ws_dev) + 256);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess && ctx->n_dual > 0) e = cudaMemsetAsync(q_dev, 0, sizeof(double) * (size_t)ctx->n_dual, st);
+  if (e == cudaSuccess && ctx->n_items > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->n_items * kCluster));
+    cfg.blockDim = dim3(kThreadsI);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = ctx->sizes.n_cluster_subdomains > 0 ? 1 : 0;   // no cluster when no item needs one
+    e = cudaLaunchKernelEx(&cfg, implicit_kernel, ctx->ptrs(), L_values_dev, lambda_dev, q_dev, X, status);
+  }
+  if (e != cudaSuccess) return ifail(ctx, SC_ERR_CUDA, std::string("sci_apply: ") + cudaGetErrorString(e));
+  return SC_OK;
+}
+
+sc_status sci_device_status(sci_ctx *ctx, const void *ws_dev, void *stream) {
+  if (!ctx || !ws_dev) return SC_ERR_INVALID_ARG;
+  uint32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ws_dev, sizeof(h), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return ifail(ctx, SC_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  if (h & 1u) return ifail(ctx, SC_ERR_NOT_SPD, "a diagonal entry of L is not positive and finite");
+  return h ? ifail(ctx, SC_ERR_INTERNAL, "unknown device status bits") : SC_OK;
+}
+
+sc_status sci_export_plan(const sci_ctx *ctx, void *dst, size_t bytes) {
+  if (!ctx || !dst || bytes < ctx->blob.size()) return SC_ERR_INVALID_ARG;
+  std::memcpy(dst, ctx->blob.data(), ctx->blob.size());
+  return SC_OK;
+}
+
+const char *sci_last_error(const sci_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+void sci_destroy(sci_ctx *ctx) { delete ctx; }
+
+}  // extern "C"

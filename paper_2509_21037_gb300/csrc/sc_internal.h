@@ -15,6 +15,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sc.h"
@@ -70,6 +71,25 @@ struct Seed {
 struct ApplyTask {
   int32_t sub, I;
 };
+
+// Symbolic analysis of one subdomain (sc_plan.cpp, steps 1-5): validated
+// patterns, fundamental supernodes of L and the pivot-sorted B^T columns.
+struct SubPlan {
+  // supernodes (local)
+  std::vector<int32_t> sn_c0, sn_ns, sn_rs, sn_jlo, sn_jhi;
+  std::vector<int64_t> sn_rows_off;  // offset of pattern(c0) in L_rowind
+  std::vector<int32_t> snode_of;     // column -> supernode
+  std::vector<int32_t> sparent;
+  std::vector<int32_t> perm_cols;    // sorted -> original column
+  // within-supernode pivot cut: columns entering s from below (entry row 0)
+  // and columns whose first nonzero on s is at local row e > 0
+  std::vector<int32_t> maxq0;
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> inner;
+};
+
+// Returns an empty string on success, else the reason (prefixed "subdomain idx: ").
+// A supernode s is reached (Y is nonzero on it) iff sn_jhi[s] > sn_jlo[s].
+std::string analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P);
 
 // Device pointers into the uploaded plan blob.
 struct PlanPtrs {

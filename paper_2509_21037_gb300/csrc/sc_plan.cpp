@@ -44,19 +44,6 @@ sc_status fail(sc_ctx *ctx, sc_status st, const std::string &msg) {
 
 namespace {
 
-struct SubPlan {
-  // supernodes (local)
-  std::vector<int32_t> sn_c0, sn_ns, sn_rs, sn_jlo, sn_jhi;
-  std::vector<int64_t> sn_rows_off;  // offset of pattern(c0) in L_rowind
-  std::vector<int32_t> snode_of;     // column -> supernode
-  std::vector<int32_t> sparent;
-  std::vector<int32_t> perm_cols;    // sorted -> original column
-  // within-supernode pivot cut: columns entering s from below (entry row 0)
-  // and columns whose first nonzero on s is at local row e > 0
-  std::vector<int32_t> maxq0;
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> inner;
-};
-
 // cut for local rows [kb, kb + 32): one past the last sorted column that is
 // nonzero somewhere in those rows (columns at or after it are zero there)
 static int32_t block_cut(const SubPlan &P, int32_t s, int32_t kb) {
@@ -78,8 +65,10 @@ size_t add_section(std::vector<uint8_t> &blob, Section &s, const std::vector<T> 
 
 std::string sub_msg(int32_t i, const std::string &m) { return "subdomain " + std::to_string(i) + ": " + m; }
 
+}  // namespace
+
 // Steps 1-5 for one subdomain.  Returns empty string on success.
-std::string analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
+std::string sc::analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
   const int32_t n = d.n, m = d.m;
   if (n < 0 || m < 0) return sub_msg(idx, "negative n or m");
   if (n == 0 && m > 0) return sub_msg(idx, "m > 0 with n == 0");
@@ -205,7 +194,6 @@ std::string analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
   return std::string();
 }
 
-}  // namespace
 
 sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<SubPlan> P(nsub);

@@ -10,8 +10,9 @@ import pytest
 
 import oracle
 import synth
-from paper_2509_21037_gb300 import _native, abi, host, sc
+from paper_2509_21037_gb300 import _native, abi, host, implicit, sc
 
+import implicit_emulator as ie
 import plan_emulator as pe
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -24,7 +25,7 @@ def _declared(header):
 
 
 @pytest.mark.parametrize("header,loader", [("sc.h", _native.sc_lib), ("sc_dense.h", _native.dense_lib),
-                                           ("sc_factor.h", _native.factor_lib)])
+                                           ("sc_factor.h", _native.factor_lib), ("sc_implicit.h", _native.sc_lib)])
 def test_library_exports_every_declared_symbol(header, loader):
     names = _declared(header)
     assert names, header
@@ -36,6 +37,7 @@ def test_library_exports_every_declared_symbol(header, loader):
 def test_binding_covers_header():
     assert _declared("sc.h") == set(abi.SC_SYMBOLS)
     assert _declared("sc_dense.h") == set(abi.DENSE_SYMBOLS)
+    assert _declared("sc_implicit.h") == set(abi.IMPLICIT_SYMBOLS)
 
 
 def _plan_raw(descs, n_dual):
@@ -241,3 +243,95 @@ def test_workspace_waves_bound_the_workspace():
     with pytest.raises(sc.SCError) as e:
         sc.Plan(fs, prob.n_dual, ws_limit=1000)
     assert e.value.status == abi.SC_ERR_OOM
+
+
+def _general_gluing():
+    """B^T columns with several nonzeros, an empty column and duplicate dofs
+    (a general B, paper Sec. 3) on a 3D cube."""
+    import scipy.sparse as sp
+    base = synth.cube_heat_3d(parts=1, k=4).subdomains[0]
+    rng = np.random.default_rng(7)
+    n, m = base.n, 40
+    rows, cols, vals = [], [], []
+    for j in range(m):
+        if j == 11:
+            continue                                  # empty column
+        k = 3 if j % 7 == 0 else 1
+        for r in rng.choice(n, size=k, replace=False):
+            rows.append(r); cols.append(j); vals.append(rng.choice([-1.0, 1.0]))
+    rows.append(rows[0]); cols.append(39); vals.append(1.0)   # a dof shared by two columns
+    Bt = sp.csc_matrix((vals, (rows, cols)), shape=(n, m))
+    sd = synth.Subdomain(K=base.K, fixed=base.fixed, Bt=Bt, lambda_map=np.arange(m), grid=base.grid,
+                         ndpn=1, key=None)
+    return synth.Problem("general", [sd], m, 0)
+
+
+def _implicit_cases():
+    yield from _cases()
+    yield "chain", synth.Problem("chain", [synth.chain_1d(40, [3, 17, 40])], 3, 0)
+    yield "cube_2x8", synth.cube_heat_3d(2, 8)         # 81-column top separators: three 32-column blocks
+
+
+@pytest.mark.parametrize("name,prob", list(_implicit_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_implicit_plan_emulation_matches_oracle(name, prob):
+    """The GPU implicit apply's plan (levels, panels, B^T gather/scatter),
+    replayed on the CPU with the kernel's index formulas, gives F*lambda."""
+    fs = host.factorize_problem(prob.subdomains)
+    ip = implicit.ImplicitPlan(fs, prob.n_dual)
+    T = ie.export_plan(ip)
+    Loff = np.concatenate([[0], np.cumsum([f.L.values.size for f in fs])])
+    assert ip.sizes.L_values == Loff[-1]
+    ie.check_bounds(T, ip.sizes, Loff, prob.n_dual)
+    lam = np.random.default_rng(5).standard_normal(prob.n_dual)
+    q = ie.emulate(T, ip.sizes, sc.concat_L_values(fs), lam, prob.n_dual)
+    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains), [s.lambda_map for s in prob.subdomains],
+                           lam, prob.n_dual)
+    assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+    # visited entries and levels are what the plan claims
+    sns = T["sns"]
+    nnz = sum(int(s["ns"]) * (int(s["ns"]) + 1) // 2 + int(s["ns"]) * int(s["rs"]) for s in sns)
+    assert ip.sizes.nnz_visited == nnz and ip.sizes.flops == 4.0 * nnz
+
+
+def test_implicit_plan_general_gluing_and_order():
+    prob = _general_gluing()
+    fs = host.factorize_problem(prob.subdomains)
+    ip = implicit.ImplicitPlan(fs, prob.n_dual)
+    T = ie.export_plan(ip)
+    Loff = np.concatenate([[0], np.cumsum([f.L.values.size for f in fs])])
+    ie.check_bounds(T, ip.sizes, Loff, prob.n_dual)
+    lam = np.random.default_rng(2).standard_normal(prob.n_dual)
+    q = ie.emulate(T, ip.sizes, sc.concat_L_values(fs), lam, prob.n_dual)
+    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains), [s.lambda_map for s in prob.subdomains],
+                           lam, prob.n_dual)
+    assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+
+
+def test_implicit_cluster_items():
+    """Automatic rule: large subdomains get a cluster each, small ones are
+    packed eight to a cluster; 0 and a huge threshold select all / none."""
+    prob = synth.mixed_batch(lat2d=(4, 4), k2d=(6, 40), lat3d=(2, 2, 1), k3d=(2, 6), seed=2)
+    fs = host.factorize_problem(prob.subdomains)
+    Loff = np.concatenate([[0], np.cumsum([f.L.values.size for f in fs])])
+    nnz = implicit.ImplicitPlan(fs, prob.n_dual).sizes.nnz_visited
+    for cmw, kinds in ((0, {0}), (1 << 60, {1}), (1, {0}), (nnz // 40, {0, 1})):
+        ip = implicit.ImplicitPlan(fs, prob.n_dual, cluster_min_work=cmw)
+        T = ie.export_plan(ip)
+        ie.check_bounds(T, ip.sizes, Loff, prob.n_dual)
+        got = set(int(k) for k in T["items"]["kind"])
+        if kinds is not None:
+            assert got == kinds, (cmw, got)
+        assert ip.sizes.n_cluster_subdomains == int(np.sum(T["items"]["kind"] == 0))
+
+
+def test_implicit_plan_subdomain_order_and_validation():
+    prob = synth.elasticity_cubes((2, 1, 1), 2, 4, seed=3)
+    fs = host.factorize_problem(prob.subdomains)
+    ip = implicit.ImplicitPlan(fs, prob.n_dual)
+    T = ie.export_plan(ip)
+    work = [int(np.sum(T["sns"][sd["sn_lo"]:sd["sn_hi"]]["ns"] * (T["sns"][sd["sn_lo"]:sd["sn_hi"]]["ns"] + 1) // 2
+                       + T["sns"][sd["sn_lo"]:sd["sn_hi"]]["ns"] * T["sns"][sd["sn_lo"]:sd["sn_hi"]]["rs"]))
+            for sd in T["subs"]]
+    assert work == sorted(work, reverse=True), "subdomains are launched largest first"
+    with pytest.raises(sc.SCError, match="lambda_map out of range"):
+        implicit.ImplicitPlan(fs, prob.n_dual - 1 if prob.n_dual > 1 else 0)
