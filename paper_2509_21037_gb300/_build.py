@@ -4,6 +4,8 @@ Produces, next to this file in ``_lib/``:
   libsc.so        -- the Schur-complement C ABI (include/sc.h), CUDA kernels
   libsc_dense.so  -- dense cuBLAS TRSM+SYRK comparator (include/sc_dense.h)
   libscfactor.so  -- host sparse Cholesky input producer (include/sc_factor.h)
+  libscpipe.so    -- CPU/GPU pipeline of the numeric stage (include/sc_pipeline.h),
+                     linked against the two above
 Translation units compile in parallel; one -gencode (sm_103a) only.
 """
 from __future__ import annotations
@@ -64,6 +66,8 @@ def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
         o = os.path.join(OBJ, s + ".o")
         objs_main.append(o)
         cmds.append(_nvcc_obj(os.path.join(CSRC, s), o, list(extra_nvcc)))
+    o_pipe = os.path.join(OBJ, "sc_pipeline.cpp.o")
+    cmds.append(_nvcc_obj(os.path.join(CSRC, "sc_pipeline.cpp"), o_pipe, list(extra_nvcc)))
     o_dense = os.path.join(OBJ, "sc_dense.cu.o")
     cmds.append(_nvcc_obj(os.path.join(CSRC, "sc_dense.cu"), o_dense, list(extra_nvcc)))
     cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-I", INC,
@@ -80,6 +84,8 @@ def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
          "-lcudart", "-lcublas"],
     ]
     _run_parallel(links)
+    _run_parallel([[nvcc, *ARCH, "-shared", o_pipe, "-o", os.path.join(OUT, "libscpipe.so"), "-L", OUT, "-lsc",
+                    "-lscfactor", "-lcudart", "-Xlinker", "-rpath,$ORIGIN"]])
     return OUT
 
 

@@ -57,6 +57,17 @@ def sc_lib() -> ctypes.CDLL:
     return lib
 
 
+def pipe_lib() -> ctypes.CDLL:
+    sc_lib()
+    factor_lib()
+    lib = _load("libscpipe.so")
+    if not getattr(lib, "_typed", False):
+        from . import abi
+        abi.declare_pipeline(lib)
+        lib._typed = True
+    return lib
+
+
 def dense_lib() -> ctypes.CDLL:
     lib = _load("libsc_dense.so")
     if not getattr(lib, "_typed", False):

@@ -85,6 +85,30 @@ IMPLICIT_SYMBOLS = {
     "sci_destroy": ([c_vp], None),
 }
 
+class PipeSubdomain(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("K_colptr", c_vp), ("K_rowind", c_vp), ("K_val", c_vp), ("nfixed", c_i32),
+                ("fixed", c_vp), ("perm", c_vp)]
+
+
+class PipeChunk(ctypes.Structure):
+    _fields_ = [("lo", c_i32), ("hi", c_i32), ("plan", c_vp), ("L_dev", c_vp), ("F_dev", c_vp),
+                ("ws_dev", c_vp), ("ws_bytes", c_sz)]
+
+
+class PipeTimes(ctypes.Structure):
+    _fields_ = [("wall_ms", ctypes.c_double), ("factor_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
+                ("assembly_ms", ctypes.c_double), ("serial_ms", ctypes.c_double), ("h2d_bytes", c_i64)]
+
+
+# every symbol include/sc_pipeline.h declares
+PIPELINE_SYMBOLS = {
+    "scp_create": ([ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(PipeSubdomain), c_i32, ctypes.POINTER(PipeChunk),
+                    c_i32], c_int),
+    "scp_run": ([c_vp, c_vp, ctypes.POINTER(PipeTimes)], c_int),
+    "scp_last_error": ([c_vp], ctypes.c_char_p),
+    "scp_destroy": ([c_vp], None),
+}
+
 DENSE_SYMBOLS = {
     "scd_create": ([ctypes.POINTER(c_vp), c_i32], c_int),
     "scd_trsm_syrk": ([c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
@@ -102,6 +126,10 @@ def _declare(lib, table):
 def declare(lib):
     _declare(lib, SC_SYMBOLS)
     _declare(lib, IMPLICIT_SYMBOLS)
+
+
+def declare_pipeline(lib):
+    _declare(lib, PIPELINE_SYMBOLS)
 
 
 def declare_dense(lib):

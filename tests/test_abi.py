@@ -25,7 +25,8 @@ def _declared(header):
 
 
 @pytest.mark.parametrize("header,loader", [("sc.h", _native.sc_lib), ("sc_dense.h", _native.dense_lib),
-                                           ("sc_factor.h", _native.factor_lib), ("sc_implicit.h", _native.sc_lib)])
+                                           ("sc_factor.h", _native.factor_lib), ("sc_implicit.h", _native.sc_lib),
+                                           ("sc_pipeline.h", _native.pipe_lib)])
 def test_library_exports_every_declared_symbol(header, loader):
     names = _declared(header)
     assert names, header
@@ -38,6 +39,7 @@ def test_binding_covers_header():
     assert _declared("sc.h") == set(abi.SC_SYMBOLS)
     assert _declared("sc_dense.h") == set(abi.DENSE_SYMBOLS)
     assert _declared("sc_implicit.h") == set(abi.IMPLICIT_SYMBOLS)
+    assert _declared("sc_pipeline.h") == set(abi.PIPELINE_SYMBOLS)
 
 
 def _plan_raw(descs, n_dual):
@@ -335,3 +337,55 @@ def test_implicit_plan_subdomain_order_and_validation():
     assert work == sorted(work, reverse=True), "subdomains are launched largest first"
     with pytest.raises(sc.SCError, match="lambda_map out of range"):
         implicit.ImplicitPlan(fs, prob.n_dual - 1 if prob.n_dual > 1 else 0)
+
+
+def test_pipeline_refactorisation_reproduces_the_planned_factor():
+    """The pipeline refactorises with the final ordering and no further
+    reordering; that must give the very L the plans were made for."""
+    prob = synth.elasticity_cubes((2, 1, 1), 2, 4, seed=1)
+    fs = host.factorize_problem(prob.subdomains)
+    for sd, f in zip(prob.subdomains, fs):
+        g = host.factorize(sd.K, sd.fixed, perm=f.L.perm, postorder=False)
+        assert np.array_equal(g.colptr, f.L.colptr) and np.array_equal(g.rowind, f.L.rowind)
+        assert np.array_equal(g.values, f.L.values)
+
+
+def test_pipeline_create_validates_chunks():
+    """Chunks must cover every subdomain once and match their plans (checked
+    before any CUDA call)."""
+    lib = _native.pipe_lib()
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    nsub = len(fs)
+    p0, p1 = sc.Plan(fs[:4], prob.n_dual), sc.Plan(fs[4:], prob.n_dual)
+    subs = (abi.PipeSubdomain * nsub)()
+    keep = []
+    for i, (sd, f) in enumerate(zip(prob.subdomains, fs)):
+        K = sd.K.tocsc()
+        K.sort_indices()
+        arrs = [np.ascontiguousarray(K.indptr, np.int64), np.ascontiguousarray(K.indices, np.int32),
+                np.ascontiguousarray(K.data), np.ascontiguousarray(sd.fixed, np.int32),
+                np.ascontiguousarray(f.L.perm, np.int32)]
+        keep += arrs
+        subs[i].n = K.shape[0]
+        subs[i].K_colptr, subs[i].K_rowind, subs[i].K_val = [a.ctypes.data for a in arrs[:3]]
+        subs[i].nfixed, subs[i].fixed, subs[i].perm = len(arrs[3]), arrs[3].ctypes.data, arrs[4].ctypes.data
+
+    def run(ranges, plans):
+        ch = (abi.PipeChunk * len(ranges))()
+        for c, ((lo, hi), p) in enumerate(zip(ranges, plans)):
+            ch[c].lo, ch[c].hi, ch[c].plan = lo, hi, p.h.value
+            ch[c].L_dev = ch[c].F_dev = ch[c].ws_dev = 256       # never dereferenced: validation fails first
+            ch[c].ws_bytes = 1 << 40
+        h = ctypes.c_void_p()
+        st = lib.scp_create(ctypes.byref(h), nsub, subs, len(ranges), ch, 2)
+        msg = lib.scp_last_error(h).decode()
+        lib.scp_destroy(h)
+        return st, msg
+
+    st, msg = run([(0, 4)], [p0])
+    assert st == abi.SC_ERR_INVALID_ARG and "exactly one chunk" in msg
+    st, msg = run([(0, 3), (3, nsub)], [p0, p1])
+    assert st == abi.SC_ERR_INVALID_ARG and "hi - lo" in msg
+    st, msg = run([(0, 4), (2, nsub)], [p0, p1])
+    assert st == abi.SC_ERR_INVALID_ARG
