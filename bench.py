@@ -225,6 +225,24 @@ def _pipeline_section(args, prob, fs, dev, stream):
     return out
 
 
+def _feti_section(prob, fs, dev, t_asm, t_expl, t_gimpl, t_himpl):
+    """FETI-1 PCPG on the bench batch (feti.py): iterations to a 1e-10
+    projected residual with and without the lumped preconditioner, and what a
+    solve of that many iterations costs with the explicit operator (assembly +
+    applications) against the GPU and host implicit applications."""
+    from paper_2509_21037_gb300 import feti
+    loads = feti.compatible_loads(prob, seed=1)
+    out = {}
+    for pc in ("lumped", "none"):
+        res = feti.FETISolver(prob, fs, device=dev, precond=pc).solve(loads, tol=1e-10)
+        n = res.iterations
+        out[pc] = {"iterations": n, "pcpg_ms": res.solve_ms, "F_apply_ms": res.apply_ms,
+                   "continuity": res.continuity, "equilibrium": res.equilibrium,
+                   "explicit_total_ms": t_asm + n * t_expl, "implicit_gpu_total_ms": n * t_gimpl,
+                   "implicit_host_total_ms": n * t_himpl}
+    return out
+
+
 def run_sc(args):
     import torch
     import torch.distributed as dist
@@ -394,6 +412,8 @@ def run_sc(args):
         "gpu_launches": args.steps * 5,
         "clocks": clocks.summary(),
     }
+    if args.feti and rank == 0:
+        line["feti_pcpg"] = _feti_section(prob, fs, dev, t_asm, t_expl, t_gimpl, t_impl)
     if args.pipeline_chunks > 0 and rank == 0:
         line["assembly_pipeline"] = _pipeline_section(args, prob, fs, dev, stream)
     if args.split and rank == 0:
@@ -597,6 +617,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-dense", dest="dense", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-feti", dest="feti", action="store_false",
+                    help="skip the FETI-1 PCPG section (iteration counts against the amortisation point)")
     ap.add_argument("--pipeline-chunks", type=int, default=4,
                     help="chunks of the CPU/GPU numeric-stage pipeline section (0: skip it)")
     ap.add_argument("--no-split", dest="split", action="store_false",
