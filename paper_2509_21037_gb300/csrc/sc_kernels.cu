@@ -128,11 +128,12 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const 
       __syncthreads();
       if (lane < wk) {
         for (int p = kb + kw + warp; p < nrow; p += kThreads / 32) {
-          double acc = 0.0;
-#pragma unroll 8
-          for (int q = 0; q < kw; ++q) acc = fma(Lv[cps[q] + p], Xs[q][lane], acc);
+          // the target row is the accumulator: no separate subtraction on the FP64 pipe
           double *tg = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
-          tg[lane] -= acc;
+          double acc = tg[lane];
+#pragma unroll 8
+          for (int q = 0; q < kw; ++q) acc = fma(-Lv[cps[q] + p], Xs[q][lane], acc);
+          tg[lane] = acc;
         }
       }
       __syncthreads();

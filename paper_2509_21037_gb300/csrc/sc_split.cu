@@ -429,10 +429,10 @@ __global__ void __launch_bounds__(kThreads, 4) trsm_split_kernel(const PlanPtrs 
             if (rr < nb && col < wk) {
               const int p = kb + kw + rr;
               const int e = (((r & 2) ? eb : ea) - 1022) + (emaxX[col] - 1022);
-              double v = gr[r].value_block();
-              v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
+              const double v = gr[r].value_block();
               double *tgt = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
-              tgt[col] -= v;
+              if (e >= -1022 && e <= 1023) tgt[col] = fma(-v, pow2i(e), tgt[col]);   // one FP64 op
+              else tgt[col] -= ldexp(v, e);
             }
           }
         }
