@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, cons
 // planes.  Warp w computes rows 16*(w>>1).. and columns 16*(w&1).. of the
 // block as two m16n8 tiles.
 template <int S>
-__global__ void __launch_bounds__(kThreads, 3) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
+// 4 resident CTAs for up to 5 digits, 3 for 6 and 7 (register-bound fragments)
+__global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
                                                               int64_t yd_plane, const int *__restrict__ colexp,
                                                               double *__restrict__ F) {
   __shared__ __align__(16) __nv_bfloat16 PA[S][32][kPad];   // [t][column of J1][k]
@@ -308,7 +309,9 @@ __global__ void __launch_bounds__(kThreads, 3) syrk_split_kernel(const PlanPtrs 
 // bounds, shared memory) and of L's rows (pre-cut by lpack_kernel), combined
 // exactly in integers and subtracted from Y in FP64.
 template <int S>
-__global__ void __launch_bounds__(kThreads, 4) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+// 6 resident CTAs for up to 5 digits (the TRSM is latency-bound: more warps
+// hide the L digit and Y loads), 4 for 6 and 7 digits (their fragments would spill)
+__global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
                                                               const double *__restrict__ invd,
                                                               const __nv_bfloat16 *__restrict__ Ld,
                                                               const int16_t *__restrict__ lexp, int64_t ld_rows,
