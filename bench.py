@@ -41,6 +41,19 @@ UNIT = "assemblies/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+def _measured_hbm_gbps() -> float:
+    """HBM copy bandwidth measured on this GPU model (MEASURED_PEAKS.json),
+    else the machine's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBPS = _measured_hbm_gbps()
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -312,6 +325,9 @@ def run_sc(args):
     value = world * nsub / (ms / 1e3)
 
     if args.profile:
+        for _ in range(args.warmup + args.steps):
+            plan.apply_fixed(F, lam, q, stream)
+        torch.cuda.synchronize(dev)
         if args.profile_implicit:
             from paper_2509_21037_gb300 import implicit
             ip = implicit.ImplicitPlan(fs, prob.n_dual).upload(dev)
@@ -366,6 +382,23 @@ def run_sc(args):
     a1.record(stream)
     a1.synchronize()
     t_expl = a0.elapsed_time(a1) / 20
+    # the same product on the integer pipes (sc_apply_fixed)
+    qf = torch.empty_like(q)
+    plan.apply_fixed(F, lam, qf, stream)
+    a0.record(stream)
+    for _ in range(20):
+        plan.apply_fixed(F, lam, qf, stream)
+    a1.record(stream)
+    a1.synchronize()
+    t_fixed = a0.elapsed_time(a1) / 20
+    apply_sec = {
+        "bytes": st["bytes_apply"],
+        "fp64": {"ms": t_expl, "GBps": st["bytes_apply"] / (t_expl / 1e3) / 1e9,
+                 "frac_hbm": st["bytes_apply"] / (t_expl / 1e3) / 1e9 / HBM_PEAK_GBPS},
+        "fixed": {"ms": t_fixed, "GBps": st["bytes_apply"] / (t_fixed / 1e3) / 1e9,
+                  "frac_hbm": st["bytes_apply"] / (t_fixed / 1e3) / 1e9 / HBM_PEAK_GBPS,
+                  "rel_diff_vs_fp64": (torch.linalg.vector_norm(qf - q) / torch.linalg.vector_norm(q)).item()},
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     t_gimpl, gimpl = _gpu_implicit(fs, prob.n_dual, Lv, lam, q, stream)
     impl = host.ImplicitApply(fs, prob.n_dual)
     lam_h = lam.cpu().numpy()
@@ -407,7 +440,9 @@ def run_sc(args):
                          "t_assembly_ms": t_asm, "t_apply_explicit_gpu_ms": t_expl,
                          "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count(),
                          "iterations_vs_gpu_implicit": t_asm / (t_gimpl - t_expl) if t_gimpl > t_expl else None,
-                         "t_apply_implicit_gpu_ms": t_gimpl},
+                         "t_apply_implicit_gpu_ms": t_gimpl,
+                         "iterations_vs_gpu_implicit_fixed_apply": t_asm / (t_gimpl - t_fixed) if t_gimpl > t_fixed else None},
+        "sc_apply": apply_sec,
         "gpu_implicit_apply": gimpl,
         "gpu_launches": args.steps * 5,
         "clocks": clocks.summary(),
@@ -548,9 +583,18 @@ def run_config5(args):
             c.synchronize()
             asm.append(a.elapsed_time(b))
             app.append(b.elapsed_time(c))
+        qf = torch.empty_like(lam)
+        b.record()
+        for _ in range(args.steps):
+            plan.apply_fixed(F, lam, qf)
+        c.record()
+        c.synchronize()
+        fx = b.elapsed_time(c) / args.steps
         out = {"assembly_ms": sum(asm) / len(asm), "apply_ms": sum(app) / len(app),
                "waves": int(plan.stats.n_waves), "ws_GB": plan.sizes.ws_bytes / 1e9,
-               "apply_GBps": plan.stats.bytes_apply / (sum(app) / len(app) / 1e3) / 1e9}
+               "apply_GBps": plan.stats.bytes_apply / (sum(app) / len(app) / 1e3) / 1e9,
+               "apply_fixed_ms": fx, "apply_fixed_GBps": plan.stats.bytes_apply / (fx / 1e3) / 1e9,
+               "apply_fixed_rel_diff": (torch.linalg.vector_norm(qf - q) / torch.linalg.vector_norm(q)).item()}
         F_off = plan.F_offsets.copy()
         st = plan.stats_dict()
         out["q"] = q

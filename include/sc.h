@@ -225,6 +225,19 @@ sc_status sc_device_status(sc_ctx *ctx, const void *ws_dev, void *stream);
 sc_status sc_apply(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
                    void *stream);
 
+/* The same product with the multiply-adds on the integer pipes (GB300's FP64
+ * pipe bounds sc_apply): every stored 32x32 tile of F and every 32-entry block
+ * of lambda is cut to 53-bit fixed point against its own largest exponent,
+ * the fixed-point values are split into two 27-bit limbs, the tile-vector
+ * products are formed exactly with 32x32 -> 64-bit integer multiply-adds
+ * and rounded to FP64 once per row and tile.  Error: about 2^-52 of
+ * 32 max|tile| max|block| per row and tile (an FP64 GEMV's rounding is of
+ * the same size).  Same arguments, layout and asynchrony as sc_apply; q is
+ * overwritten.  The paper's Eq. "dualop_apply_expl"; the fixed-point form is
+ * this library's. */
+sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
+                         void *stream);
+
 /* Expand F_i into a dense full m_i x m_i column-major device matrix dst_dev
  * with leading dimension ld >= m_i.  Asynchronous on `stream`. */
 sc_status sc_export_F(sc_ctx *ctx, const double *F_dev, int32_t i, double *dst_dev, int32_t ld,

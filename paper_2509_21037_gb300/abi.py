@@ -53,6 +53,7 @@ SC_SYMBOLS = {
     "sc_device_status": ([c_vp, c_vp, c_vp], c_int),
     "sc_assemble_batch_static": ([c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_apply_fixed": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_export_F": ([c_vp, c_vp, c_i32, c_vp, c_i32, c_vp], c_int),
     "sc_enable_stage_timing": ([c_vp, c_i32], c_int),
     "sc_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), c_i32], c_int),

@@ -117,6 +117,11 @@ class Plan:
     def apply(self, F, lam, q, stream=None):
         self._check(self.lib.sc_apply(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(), _stream_ptr(stream)))
 
+    def apply_fixed(self, F, lam, q, stream=None):
+        """q = F * lambda on the integer pipes (include/sc.h, sc_apply_fixed)."""
+        self._check(self.lib.sc_apply_fixed(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(),
+                                            _stream_ptr(stream)))
+
     def export(self, F, i: int, dst=None, stream=None):
         import torch
         m = self.m[i]
