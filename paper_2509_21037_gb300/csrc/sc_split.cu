@@ -140,14 +140,28 @@ __global__ void __launch_bounds__(kThreads) lpack_kernel(const PlanPtrs P, const
       e = max(e, biased_exponent(v[q]));
     }
     lexp[base + r] = (int16_t)e;
+    uint64_t X[32];
+    uint32_t neg = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      X[q] = fixed_point(v[q], e);                  // once per entry, not once per digit plane
+      neg |= (v[q] < 0.0 ? 1u : 0u) << q;
+    }
 #pragma unroll
     for (int d = 0; d < S; ++d) {
-      uint32_t *row = reinterpret_cast<uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + r) * 32);
+      // the row's 64 bytes of this plane as four 16-byte stores
+      uint4 *row = reinterpret_cast<uint4 *>(Ld + (int64_t)d * ld_rows * 32 + (base + r) * 32);
 #pragma unroll
-      for (int q = 0; q < 32; q += 2) {
-        const __nv_bfloat16 lo = digit_bf16(fixed_point(v[q], e), d, v[q] < 0.0);
-        const __nv_bfloat16 hi = digit_bf16(fixed_point(v[q + 1], e), d, v[q + 1] < 0.0);
-        row[q / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+      for (int g = 0; g < 4; ++g) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int q = 8 * g + 2 * h;
+          const __nv_bfloat16 lo = digit_bf16(X[q], d, (neg >> q) & 1u);
+          const __nv_bfloat16 hi = digit_bf16(X[q + 1], d, (neg >> (q + 1)) & 1u);
+          w[h] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        row[g] = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   }
