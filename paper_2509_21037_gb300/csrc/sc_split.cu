@@ -225,8 +225,12 @@ template <int S>
 __global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(const PlanPtrs P, const __nv_bfloat16 *__restrict__ Yd,
                                                               int64_t yd_plane, const int *__restrict__ colexp,
                                                               double *__restrict__ F) {
-  __shared__ __align__(16) __nv_bfloat16 PA[S][32][kPad];   // [t][column of J1][k]
-  __shared__ __align__(16) __nv_bfloat16 PB[S][32][kPad];   // [t][column of J2][k]
+  // two stages of the digit tiles: [stage][operand][t][column][k]; the next
+  // active 32-row block is fetched with asynchronous copies while this one
+  // is multiplied
+  extern __shared__ __align__(16) unsigned char syrk_smem[];
+  typedef __nv_bfloat16 Tile[S][32][kPad];
+  Tile *stages = reinterpret_cast<Tile *>(syrk_smem);          // stages[2 * buf + op]
   const SyrkTask t = P.syrk_tasks[blockIdx.x];
   const SubDev sd = P.subs[t.sub];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -240,23 +244,50 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(
 #pragma unroll
   for (int i = 0; i < 8; ++i) dacc[i] = 0.0;
   int blocks = 0;
-  for (int li = 0; li < t.list_len; ++li) {
-    const SnDev s = P.sns[P.syrk_list[t.list_off + li]];
-    const int npad = (s.ns + 31) / 32 * 32;
-    for (int k0 = 0; k0 < s.ns; k0 += 32) {
-      if (j1lo >= P.cuts[s.cut_off + (k0 >> 5)]) continue;
-      // 2 operands x S planes x 32 columns x 4 vectors of 8 digits
-      for (int v = tid; v < 2 * S * 32 * 4; v += kThreads) {
-        const int part = v & 3, col = (v >> 2) & 31, d = (v >> 7) % S, op = (v >> 7) / S;
-        const int j = (op == 0 ? j1lo : j2lo) + col - s.jlo;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (j >= 0 && j < s.jhi - s.jlo)
-          val = *reinterpret_cast<const uint4 *>(Yd + (int64_t)d * yd_plane + s.yd_off + (int64_t)j * npad + k0 +
-                                                 8 * part);
-        __nv_bfloat16 *dst = op == 0 ? &PA[d][col][8 * part] : &PB[d][col][8 * part];
-        *reinterpret_cast<uint4 *>(dst) = val;
+  // the active (supernode, 32-row block) pairs in order: rows of a supernode
+  // at or after its pivot cut for this chunk are zero and skipped
+  auto advance = [&](int &li, int &k0) -> bool {
+    for (;;) {
+      k0 += 32;
+      while (li < t.list_len && k0 >= P.sns[P.syrk_list[t.list_off + li]].ns) {
+        ++li;
+        k0 = 0;
       }
-      __syncthreads();
+      if (li >= t.list_len) return false;
+      const SnDev &sn = P.sns[P.syrk_list[t.list_off + li]];
+      if (j1lo < P.cuts[sn.cut_off + (k0 >> 5)]) return true;
+    }
+  };
+  // 2 operands x S planes x 32 columns x 4 vectors of 8 digits, 16 bytes each
+  auto fetch = [&](int li, int k0, int buf) {
+    const SnDev sn = P.sns[P.syrk_list[t.list_off + li]];
+    const int npad = (sn.ns + 31) / 32 * 32;
+    for (int v = tid; v < 2 * S * 32 * 4; v += kThreads) {
+      const int part = v & 3, col = (v >> 2) & 31, d = (v >> 7) % S, op = (v >> 7) / S;
+      const int j = (op == 0 ? j1lo : j2lo) + col - sn.jlo;
+      const bool in = j >= 0 && j < sn.jhi - sn.jlo;
+      const __nv_bfloat16 *src =
+          in ? Yd + (int64_t)d * yd_plane + sn.yd_off + (int64_t)j * npad + k0 + 8 * part : Yd;
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&stages[2 * buf + op][d][col][8 * part]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int li = 0, k0 = -32, buf = 0;
+  bool have = advance(li, k0);
+  if (have) fetch(li, k0, 0);
+  while (have) {
+    int nli = li, nk0 = k0;
+    const bool nhave = advance(nli, nk0);
+    if (nhave) {
+      fetch(nli, nk0, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this block's copies are done
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const Tile &PA = stages[2 * buf], &PB = stages[2 * buf + 1];
 #pragma unroll
       for (int d = 0; d < S; ++d) {
         float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
@@ -283,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(
 #pragma unroll
           for (int r = 0; r < 4; ++r) acc[nt * 4 + r].accumulate(d, __float2int_rn(c[nt][r]));
       }
-      __syncthreads();
+      __syncthreads();                // the next iteration's fetch overwrites this stage
       if (++blocks == 128) {          // int64 headroom, see acc
         blocks = 0;
 #pragma unroll
@@ -292,7 +323,10 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(
           acc[i] = Groups<S>();
         }
       }
-    }
+    li = nli;
+    k0 = nk0;
+    have = nhave;
+    buf ^= 1;
   }
   const int32_t *perm = P.perm_cols + sd.col_off;
   const int *ce = colexp + sd.col_off;
@@ -532,7 +566,12 @@ int launch_syrk_split(const sc_ctx &c, int S_, int64_t base, int64_t count, void
   const __nv_bfloat16 *Yd = reinterpret_cast<const __nv_bfloat16 *>(w + c.ws.yd_off);
   PlanPtrs p = c.ptrs();
   p.syrk_tasks += base;
-#define SY(S) syrk_split_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Yd, c.ws.yd_plane, colexp, F)
+#define SY(S)                                                                                              \
+  {                                                                                                        \
+    const int smem = (int)(4 * sizeof(__nv_bfloat16) * S * 32 * kPad);                                     \
+    cudaFuncSetAttribute(syrk_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);         \
+    syrk_split_kernel<S><<<(unsigned)count, kThreads, smem, st>>>(p, Yd, c.ws.yd_plane, colexp, F);        \
+  }
   SC_SPLIT_SWITCH(S_, SY)
 #undef SY
   return (int)cudaGetLastError();
