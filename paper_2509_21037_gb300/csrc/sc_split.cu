@@ -103,13 +103,11 @@ struct Groups {
   // |I_d| < 2^24 (one 32-row block): the sum needs 73 bits at most; drop the
   // lowest cut = 11 bits of Lo (2^-53 of the column-bound product) and
   // convert once.
-  __device__ __forceinline__ double value_block() const {
-    constexpr int sh = 8 * (S - h);
-    constexpr int bits = 24 + 8 * (S - 1) + 1;
-    constexpr int cut = bits > 62 ? bits - 62 : 0;
-    const long long T = (H << (sh - cut)) + (Lo >> cut);
-    return (double)T * pow2i(cut - 8 * (S + 1));
-  }
+  static constexpr int kBits = 24 + 8 * (S - 1) + 1;
+  static constexpr int kCut = kBits > 62 ? kBits - 62 : 0;
+  // the block value is block_int() * 2^kBlockShift
+  static constexpr int kBlockShift = kCut - 8 * (S + 1);
+  __device__ __forceinline__ long long block_int() const { return (H << (8 * (S - h) - kCut)) + (Lo >> kCut); }
   // |I_d| < 2^31 (many blocks): two conversions and one FMA
   __device__ __forceinline__ double value_wide() const {
     return fma((double)H, pow2i(8 * (S - h) - 8 * (S + 1)), (double)Lo * pow2i(-8 * (S + 1)));
@@ -480,10 +478,13 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
             if (rr < nb && col < wk) {
               const int p = kb + kw + rr;
               const int e = (((r & 2) ? eb : ea) - 1022) + (emaxX[col] - 1022);
-              const double v = gr[r].value_block();
+              // one conversion and one FMA on the FP64 pipe: both power-of-two
+              // scalings folded into a single exponent
+              const double v = (double)gr[r].block_int();
+              const int eb = e + Groups<S>::kBlockShift;
               double *tgt = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
-              if (e >= -1022 && e <= 1023) tgt[col] = fma(-v, pow2i(e), tgt[col]);   // one FP64 op
-              else tgt[col] -= ldexp(v, e);
+              if (eb >= -1022 && eb <= 1023) tgt[col] = fma(-v, pow2i(eb), tgt[col]);
+              else tgt[col] -= ldexp(v, eb);
             }
           }
         }
