@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -75,7 +76,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples (the JSON line carries their summary); SC_BENCH_CLOCKS_DIR keeps them
+        d = os.environ.get("SC_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"sc_bench_clocks_rank{index}.csv")
         self.window = None
 
     def mark(self, t0: float, t1: float):
