@@ -116,12 +116,19 @@ enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
  *            waves run one after the other and reuse the same workspace (the
  *            paper's temporary memory pool, Sec. 3.1).  SC_ERR_OOM if one
  *            subdomain alone does not fit. */
+/* persistent: 0 (default) launches one CTA per FP64 TRSM / SYRK task and
+ *            lets the hardware block scheduler hand them out; 1 launches as
+ *            many CTAs as the GPU keeps resident, which pull task indices
+ *            (largest first) from an atomic counter in the workspace status
+ *            area until the list is exhausted (a persistent work queue; no
+ *            CTA waits on another). */
 typedef struct {
   int32_t precision;
   int32_t n_slices;
   const int8_t *sub_slices;
   int64_t ws_limit;
-  int32_t reserved[2]; /* must be zero */
+  int32_t persistent;
+  int32_t reserved; /* must be zero */
 } sc_options;
 
 typedef struct {

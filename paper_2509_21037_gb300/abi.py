@@ -25,7 +25,7 @@ SC_FP64, SC_SPLIT_BF16 = 0, 1
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("sub_slices", c_vp), ("ws_limit", c_i64),
-                ("reserved", c_i32 * 2)]
+                ("persistent", c_i32), ("reserved", c_i32)]
 
 
 class Sizes(ctypes.Structure):

@@ -150,6 +150,7 @@ struct sc_ctx {
   int32_t n_slices = 0;              // largest digit count of any subdomain (plane sizing)
   std::vector<int8_t> sub_var;       // per subdomain: 0 = FP64, 3..7 = split digits
   int64_t ws_limit = 0;              // workspace bytes per wave (0 = one wave)
+  int32_t persistent = 0;            // FP64 TRSM/SYRK as work-queue kernels (sc_options.persistent)
   // per wave, launch groups by variant (index 0 = FP64, 3..7 = digits): first item, count
   struct WaveGroups {
     int64_t trsm[8][2] = {}, syrk[8][2] = {}, sblk[8][2] = {};

@@ -29,6 +29,8 @@
 // updates.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "sc_internal.h"
@@ -70,12 +72,11 @@ __global__ void fpad_kernel(const SubDev *__restrict__ subs, double *__restrict_
   }
 }
 
-__global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const double *__restrict__ Lv,
-                                                        const double *__restrict__ invd,
-                                                        double *__restrict__ Y) {
-  __shared__ double Xs[32][33];     // current 32-row block of the solved chunk, [row][column]
-  __shared__ int64_t cps[32];       // cps[q] = index of L(p, c0+kb+q) minus p
-  const TrsmTask t = P.trsm_tasks[blockIdx.x];
+// One TRSM task (a 32-column chunk of one subdomain).  Xs: the current 32-row
+// block of the solved chunk, [row][column]; cps[q] = index of L(p, c0+kb+q) minus p.
+__device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, const double *__restrict__ Lv,
+                                          const double *__restrict__ invd, double *__restrict__ Y,
+                                          double (*Xs)[33], int64_t *cps) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c_hi = t.c_lo + t.w;
 
@@ -138,6 +139,30 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const 
       }
       __syncthreads();
     }
+  }
+}
+
+// Work-queue form (queue != nullptr): a grid sized to the resident CTAs pulls
+// task indices from an atomic counter until the list is exhausted; otherwise
+// one CTA per task.  Tasks are ordered largest first by the planner.
+__global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+                                                        const double *__restrict__ invd, double *__restrict__ Y,
+                                                        unsigned *queue, int ntask) {
+  __shared__ double Xs[32][33];
+  __shared__ int64_t cps[32];
+  __shared__ int next;
+  if (!queue) {
+    trsm_task(P, P.trsm_tasks[blockIdx.x], Lv, invd, Y, Xs, cps);
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int k = next;
+    __syncthreads();
+    if (k >= ntask) break;
+    trsm_task(P, P.trsm_tasks[k], Lv, invd, Y, Xs, cps);
+    __syncthreads();
   }
 }
 
@@ -205,10 +230,9 @@ __device__ __forceinline__ void syrk_diag_block(const PlanPtrs &P, const SyrkTas
   }
 }
 
-__global__ void __launch_bounds__(kThreads) syrk_kernel(const PlanPtrs P, const double *__restrict__ Y,
-                                                        double *__restrict__ F) {
-  __shared__ double As[32][33], Bs[32][33];  // [k][column of the chunk]
-  const SyrkTask t = P.syrk_tasks[blockIdx.x];
+// One SYRK task (a 32x32 block of F); As, Bs: [k][column of the chunk]
+__device__ __forceinline__ void syrk_task(const PlanPtrs &P, const SyrkTask t, const double *__restrict__ Y,
+                                          double *__restrict__ F, double (*As)[33], double (*Bs)[33]) {
   const SubDev sd = P.subs[t.sub];
   if (t.q1 == t.q2) {
     syrk_diag_block(P, t, sd, Y, F, As);
@@ -255,6 +279,25 @@ __global__ void __launch_bounds__(kThreads) syrk_kernel(const PlanPtrs P, const 
       T[(hi % kTile) + kTile * (lo % kTile)] = acc[u];
       if (I == J) T[(lo % kTile) + kTile * (hi % kTile)] = acc[u];
     }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) syrk_kernel(const PlanPtrs P, const double *__restrict__ Y,
+                                                        double *__restrict__ F, unsigned *queue, int ntask) {
+  __shared__ double As[32][33], Bs[32][33];
+  __shared__ int next;
+  if (!queue) {
+    syrk_task(P, P.syrk_tasks[blockIdx.x], Y, F, As, Bs);
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int k = next;
+    __syncthreads();
+    if (k >= ntask) break;
+    syrk_task(P, P.syrk_tasks[k], Y, F, As, Bs);
+    __syncthreads();
   }
 }
 
@@ -317,6 +360,16 @@ __global__ void export_kernel(const SubDev *__restrict__ subs, int32_t i, const 
 
 static inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
+// CTAs of `kernel` (kThreads threads, static shared memory) the GPU keeps resident at once
+template <class K>
+int resident_ctas(K kernel) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0);
+  return std::max(1, sms * std::max(1, per));
+}
+
 int launch_prep(const sc_ctx &c, const double *Lv, double *invd, uint32_t *status, double *F, void *ws,
                 void *stream) {
   const PlanPtrs p = c.ptrs();
@@ -340,7 +393,16 @@ int launch_group_trsm(const sc_ctx &c, int w, int v, const double *Lv, const dou
     if (G.trsm[0][1] > 0) {
       PlanPtrs p = c.ptrs();
       p.trsm_tasks += G.trsm[0][0];
-      trsm_kernel<<<(unsigned)G.trsm[0][1], kThreads, 0, S(stream)>>>(p, Lv, invd, Y);
+      const int n = (int)G.trsm[0][1];
+      if (c.persistent) {
+        unsigned *q = reinterpret_cast<unsigned *>(static_cast<uint8_t *>(ws) + c.ws.status_off + 64);
+        cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned), S(stream));
+        if (e != cudaSuccess) return (int)e;
+        const int grid = std::min(n, resident_ctas(trsm_kernel));
+        trsm_kernel<<<(unsigned)grid, kThreads, 0, S(stream)>>>(p, Lv, invd, Y, q, n);
+      } else {
+        trsm_kernel<<<(unsigned)n, kThreads, 0, S(stream)>>>(p, Lv, invd, Y, nullptr, n);
+      }
     }
     return (int)cudaGetLastError();
   }
@@ -356,7 +418,16 @@ int launch_group_syrk(const sc_ctx &c, int w, int v, const double *Y, void *ws, 
     if (G.syrk[0][1] > 0) {
       PlanPtrs p = c.ptrs();
       p.syrk_tasks += G.syrk[0][0];
-      syrk_kernel<<<(unsigned)G.syrk[0][1], kThreads, 0, S(stream)>>>(p, Y, F);
+      const int n = (int)G.syrk[0][1];
+      if (c.persistent) {
+        unsigned *q = reinterpret_cast<unsigned *>(static_cast<uint8_t *>(ws) + c.ws.status_off + 128);
+        cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned), S(stream));
+        if (e != cudaSuccess) return (int)e;
+        const int grid = std::min(n, resident_ctas(syrk_kernel));
+        syrk_kernel<<<(unsigned)grid, kThreads, 0, S(stream)>>>(p, Y, F, q, n);
+      } else {
+        syrk_kernel<<<(unsigned)n, kThreads, 0, S(stream)>>>(p, Y, F, nullptr, n);
+      }
     }
     return (int)cudaGetLastError();
   }

@@ -615,6 +615,8 @@ sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomain
     ctx->precision = ctx->n_slices > 0 ? SC_SPLIT_BF16 : SC_FP64;
     if (opt && opt->ws_limit < 0) st = fail(ctx, SC_ERR_INVALID_ARG, "ws_limit < 0");
     ctx->ws_limit = opt ? opt->ws_limit : 0;
+    if (opt && opt->persistent != 0 && opt->persistent != 1) st = fail(ctx, SC_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    ctx->persistent = opt ? opt->persistent : 0;
   }
   if (st == SC_OK && !(nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0)) {
     ctx->nsub = nsub;

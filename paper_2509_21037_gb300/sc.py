@@ -35,7 +35,7 @@ class Plan:
     """
 
     def __init__(self, subdomains: Sequence, n_dual: int, precision: int = abi.SC_FP64, n_slices: int = 0,
-                 sub_slices: Optional[Sequence[int]] = None, ws_limit: int = 0):
+                 sub_slices: Optional[Sequence[int]] = None, ws_limit: int = 0, persistent: bool = False):
         self.lib = _native.sc_lib()
         self.nsub = len(subdomains)
         self.n_dual = int(n_dual)
@@ -55,6 +55,7 @@ class Plan:
         opt.precision = precision
         opt.n_slices = n_slices
         opt.ws_limit = int(ws_limit)
+        opt.persistent = int(bool(persistent))
         if sub_slices is not None:
             self._sub_slices = np.ascontiguousarray(np.asarray(sub_slices), dtype=np.int8)
             assert len(self._sub_slices) == self.nsub

@@ -352,3 +352,28 @@ def test_config5_full_size_sampled(dev):
           f"kernel vs exact-with-L {oracle.relative_frobenius(Fg, FL):.3e}")
     assert err <= floor + TOL
     assert oracle.relative_frobenius(Fg, FL) <= TOL
+
+
+@pytest.mark.parametrize("name", ["config2", "mixed_waves"])
+def test_persistent_work_queue_bitwise(name, dev):
+    """sc_options.persistent: resident CTAs pulling tasks from an atomic
+    counter compute exactly what one CTA per task computes."""
+    if name == "config2":
+        prob = synth.make_config(2)
+        kw = {}
+    else:
+        prob = synth.mixed_batch(lat2d=(2, 2), k2d=(6, 40), lat3d=(2, 1, 1), k3d=(2, 6), seed=3)
+        kw = {}
+    fs = host.factorize_problem(prob.subdomains)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    out = []
+    for pers in (False, True):
+        one = sc.Plan(fs, prob.n_dual).upload(dev)
+        lim = one.sizes.ws_bytes // 2 if name == "mixed_waves" else 0
+        plan = sc.Plan(fs, prob.n_dual, ws_limit=lim, persistent=pers).upload(dev)
+        F = plan.new_F(dev)
+        F.fill_(float("nan"))
+        plan.assemble(Lv, F)
+        assert plan.device_status() == abi.SC_OK
+        out.append(F.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
