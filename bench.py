@@ -370,7 +370,40 @@ def run_sc(args):
         e1.record(stream)
         e1.synchronize()
         e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = sum(e_ms) / len(e_ms)
+    e2e_serial_ms = sum(e_ms) / len(e_ms)
+    # the same steps back to back as a pipeline: step k+1's L goes up on a
+    # copy stream into the other device buffer while step k assembles; every
+    # step's inputs are still copied and its result read back inside the
+    # timed region (inputs exceed L2, so no flush between steps)
+    Lbuf = [Ld, torch.empty_like(Lv)]
+    cs = torch.cuda.Stream(dev)
+    K = max(3, args.steps)
+    copied = [torch.cuda.Event() for _ in range(K)]
+    used = [torch.cuda.Event() for _ in range(K)]
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    cs.wait_event(e0)
+    with torch.cuda.stream(cs):
+        Lbuf[0].copy_(Lpin, non_blocking=True)
+        copied[0].record(cs)
+    for k in range(K):
+        if k + 1 < K:
+            with torch.cuda.stream(cs):
+                if k >= 1:
+                    cs.wait_event(used[k - 1])          # the buffer step k-1 read is free again
+                Lbuf[(k + 1) % 2].copy_(Lpin, non_blocking=True)
+                copied[k + 1].record(cs)
+        stream.wait_event(copied[k])
+        with torch.cuda.stream(stream):
+            lamd.copy_(lam_pin, non_blocking=True)
+        plan.assemble(Lbuf[k % 2], F, stream)
+        used[k].record(stream)
+        plan.apply(F, lamd, q, stream)
+        with torch.cuda.stream(stream):
+            q_pin.copy_(q, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / K
     if plan.device_status(stream) != 0:
         raise RuntimeError("device status not OK after the timed steps")
 
@@ -436,9 +469,12 @@ def run_sc(args):
                      "peak_source": "FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe FP64 1.25 TFLOP/s)"},
         "e2e": {"value": world * nsub / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(Lpin.numel() * 8 + lam_pin.numel() * 8),
-                "d2h_bytes_per_step": int(q_pin.numel() * 8)},
+                "d2h_bytes_per_step": int(q_pin.numel() * 8),
+                "note": "steps back to back; step k+1's L copy overlaps step k's assembly"},
+        "e2e_serial": {"value": world * nsub / (e2e_serial_ms / 1e3), "unit": UNIT,
+                       "note": "each step alone: copy, assemble, apply, read back"},
         "amortization": {"iterations": t_asm / (t_impl - t_expl) if t_impl > t_expl else None,
-                         "iterations_incl_L_h2d": (t_asm + (e2e_ms - ms)) / (t_impl - t_expl)
+                         "iterations_incl_L_h2d": (t_asm + (e2e_serial_ms - ms)) / (t_impl - t_expl)
                          if t_impl > t_expl else None,
                          "t_assembly_ms": t_asm, "t_apply_explicit_gpu_ms": t_expl,
                          "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count(),
