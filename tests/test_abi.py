@@ -389,3 +389,23 @@ def test_pipeline_create_validates_chunks():
     assert st == abi.SC_ERR_INVALID_ARG and "hi - lo" in msg
     st, msg = run([(0, 4), (2, nsub)], [p0, p1])
     assert st == abi.SC_ERR_INVALID_ARG
+
+
+def test_plan_rejects_bad_persistent_flag():
+    """sc_options.persistent is 0 or 1."""
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    lib = _native.sc_lib()
+    keep = []
+    d = _desc_from(fs[0], keep)
+    for flag, ok in ((0, True), (1, True), (2, False)):
+        opt = abi.Options()
+        opt.persistent = flag
+        h = ctypes.c_void_p()
+        st = lib.sc_plan(ctypes.byref(h), 1, ctypes.byref(d), prob.n_dual, ctypes.byref(opt))
+        msg = lib.sc_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib.sc_destroy(h)
+        assert (st == abi.SC_OK) == ok, (flag, st, msg)
+        if not ok:
+            assert "persistent" in msg
