@@ -60,6 +60,15 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def _max_over_ranks(ms: float, dev=None) -> float:
+    """The slowest rank's time (every rank gets it): value = all ranks' units / this."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload_config(args):
     return {"workload": "heat3d_cube_4x4x4_subdomains_16^3_hex8", "subdomains": 64, "dofs_per_subdomain": 4913,
             "multipliers_total": 39807, "precision": "fp64", "seed": args.seed,
@@ -320,9 +329,7 @@ def run_sc(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = _max_over_ranks(ms, dev)
         dist.barrier()
     nsub = len(fs)
     value = world * nsub / (ms / 1e3)
