@@ -274,3 +274,28 @@ def test_pins_catch_planted_mistakes(monkeypatch, name, bad):
     assert _pins_pass()
     monkeypatch.setattr(oracle, name, bad)
     assert not _pins_pass()
+
+
+def test_config1_anchor_golden():
+    """The oracle's config-1 F against the stored anchor (written by
+    tests/golden/make_config1_anchor.py from the oracle) and against an
+    independent dense computation's printed digits."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_anchor.txt")
+    stored = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        stored[k] = float(v)
+    F = oracle.dual_operator(synth.make_config(1).subdomains[0], refine=1)
+    ev = np.linalg.eigvalsh(0.5 * (F + F.T))
+    got = {"frobenius": np.linalg.norm(F), "trace": np.trace(F), "lambda_min": ev[0], "lambda_max": ev[-1],
+           "m": F.shape[0]}
+    for k, v in stored.items():
+        assert abs(got[k] - v) <= 1e-12 * max(1.0, abs(v)), k
+    # independent dense computation (numpy inverse of K_reg gathered by B), 4-5 printed digits
+    assert abs(got["frobenius"] - 174.9015) < 5e-5
+    assert abs(got["trace"] - 266.3118) < 5e-5
+    assert abs(got["lambda_min"] - 0.5774) < 5e-5
+    assert abs(got["lambda_max"] - 173.8) < 5e-2
