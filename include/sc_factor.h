@@ -33,9 +33,31 @@ enum { SCF_OK = 0, SCF_ERR_INVALID_ARG = 1, SCF_ERR_NOT_SPD = 2, SCF_ERR_OOM = 3
 
 typedef struct scf_factor scf_factor;
 
+/* Symbolic and numeric stage in one call: scf_analyze, then scf_numeric into
+ * the handle's own values. */
 int scf_factorize(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, const double *K_val,
                   int32_t nfixed, const int32_t *fixed, const int32_t *perm_in, int32_t do_postorder,
                   scf_factor **out);
+
+/* Symbolic stage alone (paper Sec. 2.2): ordering (perm_in, optional
+ * postorder), the pattern of L, and the map from K's stored entries to the
+ * regularised, permuted matrix.  Only K's pattern is read.  The handle's
+ * values are zero until scf_numeric writes them elsewhere; scf_export of
+ * colptr, rowind and perm is valid at once.  K_colptr must start at 0 and
+ * be non-decreasing, every row index in [0, n): SCF_ERR_INVALID_ARG
+ * otherwise. */
+int scf_analyze(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, int32_t nfixed, const int32_t *fixed,
+                const int32_t *perm_in, int32_t do_postorder, scf_factor **out);
+
+/* Numeric stage for an analysed pattern: L's values (scf_nnz doubles, the
+ * CSC layout scf_export gives) from K_val, the stored values of a K with
+ * exactly the pattern given to scf_analyze (same K_colptr, K_rowind; the
+ * values may differ from call to call).  The handle is only read, so
+ * several threads may run scf_numeric on one handle into different outputs.
+ * L_val is caller memory (host, e.g. a pinned staging buffer) and is fully
+ * overwritten on success; on SCF_ERR_NOT_SPD its contents are unspecified.
+ * Gives bit for bit the values scf_factorize gives for the same input. */
+int scf_numeric(const scf_factor *f, const double *K_val, double *L_val);
 
 /* number of stored entries of L (lower triangle incl. diagonal); -1 on NULL */
 int64_t scf_nnz(const scf_factor *f);

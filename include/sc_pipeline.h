@@ -13,13 +13,18 @@
  *
  * so that the host factorisation hides the GPU work (or the other way round)
  * instead of adding to it.  The symbolic work (ordering, sc_plan, plan
- * upload) is the initialisation stage and happens before, once.
+ * upload, and the symbolic stage of every host factorisation, scf_analyze of
+ * sc_factor.h, which scp_create runs) is the initialisation stage and
+ * happens before, once; scp_run runs only the numeric stage (scf_numeric),
+ * writing each L straight into the staging buffer.
  *
- * Inputs per subdomain (host memory, read during scp_run, owned by the
- * caller): K in full symmetric CSC (original dof order), the fixed dofs of
- * the regularisation, and the final fill-reducing ordering perm[new] = old
- * with which the chunk's plan was made (the factor is computed as
- * L L^T = P K_reg P^T with exactly this P, no further reordering).
+ * Inputs per subdomain (host memory owned by the caller): K in full
+ * symmetric CSC (original dof order), the fixed dofs of the regularisation,
+ * and the final fill-reducing ordering perm[new] = old with which the
+ * chunk's plan was made (the factor is computed as L L^T = P K_reg P^T with
+ * exactly this P, no further reordering).  K's pattern, the fixed dofs and
+ * perm are read in scp_create; K's values (K_val) are read during every
+ * scp_run, so new values on the same pattern give new factors and F.
  * Per chunk: its plan (sc_plan of exactly the subdomains [lo, hi), uploaded)
  * and device buffers for its L values (plan's L_values doubles), F and
  * workspace.  Chunks may share a workspace (they run in order on one
@@ -30,8 +35,9 @@
  * chunk's L values each), CUDA events and one copy stream per context.
  *
  * Errors: sc_status codes of sc.h.  SC_ERR_NOT_SPD when a host factorisation
- * meets a non-positive pivot; SC_ERR_INVALID_ARG when a factor's pattern does
- * not match its plan (different nnz per subdomain) or arguments are invalid;
+ * meets a non-positive pivot (scp_run); SC_ERR_INVALID_ARG when a factor's
+ * pattern does not match its plan (different nnz per subdomain) or arguments
+ * are invalid (scp_create); SC_ERR_INTERNAL when a host allocation fails;
  * SC_ERR_CUDA on a CUDA error. */
 #ifndef SC_PIPELINE_H
 #define SC_PIPELINE_H
@@ -75,8 +81,9 @@ typedef struct {
   int64_t h2d_bytes;
 } scp_times;
 
-/* nthreads <= 0: every hardware thread.  The arrays are copied (the pointers
- * inside scp_subdomain are not: the host data must outlive scp_run). */
+/* nthreads <= 0: every hardware thread (used for the symbolic stage here and
+ * the numeric stage in scp_run).  The arrays are copied (the pointers inside
+ * scp_subdomain are not: K_val must outlive every scp_run). */
 sc_status scp_create(scp_ctx **out, int32_t nsub, const scp_subdomain *subs, int32_t nchunks,
                      const scp_chunk *chunks, int32_t nthreads);
 

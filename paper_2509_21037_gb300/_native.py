@@ -36,6 +36,10 @@ def factor_lib() -> ctypes.CDLL:
     if not getattr(lib, "_typed", False):
         lib.scf_factorize.argtypes = [c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]
         lib.scf_factorize.restype = c_int
+        lib.scf_analyze.argtypes = [c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]
+        lib.scf_analyze.restype = c_int
+        lib.scf_numeric.argtypes = [c_vp, c_vp, c_vp]
+        lib.scf_numeric.restype = c_int
         lib.scf_nnz.argtypes = [c_vp]
         lib.scf_nnz.restype = c_i64
         lib.scf_export.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]

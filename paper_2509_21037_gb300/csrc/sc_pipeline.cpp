@@ -1,6 +1,9 @@
 // CPU/GPU pipeline of the numeric assembly stage (include/sc_pipeline.h):
 // host numeric factorisation of chunk c+1 overlapped with the host->device
-// copy and the GPU assembly of chunk c.
+// copy and the GPU assembly of chunk c.  The symbolic stage of every
+// subdomain's factorisation (scf_analyze) runs once in scp_create; scp_run
+// runs only the numeric stage (scf_numeric), straight into the pinned
+// staging buffer.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +23,7 @@ struct scp_ctx {
   std::string err;
   std::vector<scp_subdomain> subs;
   std::vector<scp_chunk> chunks;
+  std::vector<scf_factor *> sym;              // per subdomain: the analysed ordering and pattern of L
   std::vector<std::vector<int64_t>> L_off;   // per chunk: the plan's L offsets (hi - lo + 1)
   int32_t nthreads = 1;
   size_t stage_doubles = 0;
@@ -27,6 +31,7 @@ struct scp_ctx {
   cudaStream_t copy = nullptr;
   std::vector<cudaEvent_t> ev_copy0, ev_copy1, ev_asm0, ev_asm1;
   ~scp_ctx() {
+    for (scf_factor *f : sym) scf_free(f);
     for (double *p : stage)
       if (p) cudaFreeHost(p);
     for (auto *v : {&ev_copy0, &ev_copy1, &ev_asm0, &ev_asm1})
@@ -47,7 +52,8 @@ sc_status cuda_fail(scp_ctx *c, cudaError_t e, const char *where) {
   return pfail(c, SC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Factorise subdomains [lo, hi) into dst (the chunk's concatenated L values).
+// Numeric factorisation of subdomains [lo, hi) into dst (the chunk's
+// concatenated L values), on the analysed patterns.
 sc_status factor_chunk(scp_ctx *ctx, int32_t c, double *dst) {
   const scp_chunk &ch = ctx->chunks[c];
   const std::vector<int64_t> &off = ctx->L_off[c];
@@ -62,22 +68,13 @@ sc_status factor_chunk(scp_ctx *ctx, int32_t c, double *dst) {
       const int32_t k = next.fetch_add(1);
       if (k >= cnt || status.load() != SC_OK) return;
       const int32_t i = ch.lo + k;
-      const scp_subdomain &s = ctx->subs[i];
-      scf_factor *f = nullptr;
-      const int rc = scf_factorize(s.n, s.K_colptr, s.K_rowind, s.K_val, s.nfixed, s.fixed, s.perm, 0, &f);
+      const int rc = scf_numeric(ctx->sym[i], ctx->subs[i].K_val, dst + off[k]);
       sc_status st = SC_OK;
       std::string m;
       if (rc != SCF_OK) {
-        st = rc == SCF_ERR_NOT_SPD ? SC_ERR_NOT_SPD : SC_ERR_INVALID_ARG;
-        m = "subdomain " + std::to_string(i) + ": host factorisation failed (code " + std::to_string(rc) + ")";
-      } else if (scf_nnz(f) != off[k + 1] - off[k]) {
-        st = SC_ERR_INVALID_ARG;
-        m = "subdomain " + std::to_string(i) + ": factor has " + std::to_string(scf_nnz(f)) +
-            " entries, the plan expects " + std::to_string(off[k + 1] - off[k]);
-      } else {
-        scf_export(f, nullptr, nullptr, dst + off[k], nullptr);
+        st = rc == SCF_ERR_NOT_SPD ? SC_ERR_NOT_SPD : rc == SCF_ERR_OOM ? SC_ERR_INTERNAL : SC_ERR_INVALID_ARG;
+        m = "subdomain " + std::to_string(i) + ": host numeric factorisation failed (code " + std::to_string(rc) + ")";
       }
-      if (f) scf_free(f);
       if (st != SC_OK) {
         int expected = SC_OK;
         if (status.compare_exchange_strong(expected, st)) {
@@ -133,6 +130,39 @@ sc_status scp_create(scp_ctx **out, int32_t nsub, const scp_subdomain *subs, int
   }
   for (int32_t i = 0; i < nsub; ++i)
     if (covered[i] != 1) return pfail(ctx, SC_ERR_INVALID_ARG, "every subdomain must lie in exactly one chunk");
+  // symbolic stage of every subdomain, on the host threads; its L pattern must be the plan's
+  ctx->sym.assign(nsub, nullptr);
+  std::vector<int32_t> chunk_of(nsub), index_in(nsub);
+  for (int32_t c = 0; c < nchunks; ++c)
+    for (int32_t i = ctx->chunks[c].lo; i < ctx->chunks[c].hi; ++i) {
+      chunk_of[i] = c;
+      index_in[i] = i - ctx->chunks[c].lo;
+    }
+  std::vector<std::string> why(nsub);
+  {
+    std::atomic<int32_t> next{0};
+    auto work = [&]() {
+      for (int32_t i; (i = next.fetch_add(1)) < nsub;) {
+        const scp_subdomain &s = ctx->subs[i];
+        const int rc = scf_analyze(s.n, s.K_colptr, s.K_rowind, s.nfixed, s.fixed, s.perm, 0, &ctx->sym[i]);
+        const std::vector<int64_t> &off = ctx->L_off[chunk_of[i]];
+        const int64_t want = off[index_in[i] + 1] - off[index_in[i]];
+        if (rc != SCF_OK)
+          why[i] = "subdomain " + std::to_string(i) + ": host symbolic factorisation failed (code " +
+                   std::to_string(rc) + ")";
+        else if (scf_nnz(ctx->sym[i]) != want)
+          why[i] = "subdomain " + std::to_string(i) + ": factor has " + std::to_string(scf_nnz(ctx->sym[i])) +
+                   " entries, the plan expects " + std::to_string(want);
+      }
+    };
+    const int32_t T = std::max(1, std::min(ctx->nthreads, nsub));
+    std::vector<std::thread> pool;
+    for (int32_t t = 1; t < T; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+  }
+  for (int32_t i = 0; i < nsub; ++i)
+    if (!why[i].empty()) return pfail(ctx, SC_ERR_INVALID_ARG, why[i]);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
   for (int b = 0; b < 2; ++b) {

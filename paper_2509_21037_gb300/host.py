@@ -115,6 +115,54 @@ def factorize(K: sp.spmatrix, fixed: Sequence[int], perm: Optional[np.ndarray] =
     return out
 
 
+class SymbolicFactor:
+    """The symbolic stage alone (scf_analyze): the ordering and L's pattern
+    for K's pattern, kept so that ``numeric`` runs only the numeric stage
+    (scf_numeric) for any values on that pattern (paper Sec. 2.2)."""
+
+    def __init__(self, K: sp.spmatrix, fixed: Sequence[int], perm: Optional[np.ndarray] = None,
+                 postorder: bool = True):
+        lib = _native.factor_lib()
+        Kc = sp.csc_matrix(K)
+        Kc.sort_indices()
+        self.n = Kc.shape[0]
+        self._cp = np.ascontiguousarray(Kc.indptr, dtype=np.int64)
+        self._ri = np.ascontiguousarray(Kc.indices, dtype=np.int32)
+        fx = np.ascontiguousarray(np.asarray(fixed), dtype=np.int32)
+        pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = lib.scf_analyze(self.n, self._cp.ctypes.data, self._ri.ctypes.data, len(fx),
+                             fx.ctypes.data if len(fx) else None, pm.ctypes.data if pm is not None else None,
+                             int(postorder), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"scf_analyze failed with code {rc}")
+        self._h = h
+        nnz = lib.scf_nnz(h)
+        self.colptr = np.empty(self.n + 1, np.int64)
+        self.rowind = np.empty(nnz, np.int32)
+        self.perm = np.empty(self.n, np.int32)
+        lib.scf_export(h, self.colptr.ctypes.data, self.rowind.ctypes.data, None, self.perm.ctypes.data)
+
+    def numeric(self, K: sp.spmatrix) -> HostFactor:
+        """L for K's values; K must have the analysed pattern."""
+        Kc = sp.csc_matrix(K)
+        Kc.sort_indices()
+        if not (np.array_equal(Kc.indptr, self._cp) and np.array_equal(Kc.indices, self._ri)):
+            raise ValueError("K does not have the analysed pattern")
+        va = np.ascontiguousarray(Kc.data, dtype=np.float64)
+        values = np.empty(len(self.rowind), np.float64)
+        rc = _native.factor_lib().scf_numeric(self._h, va.ctypes.data, values.ctypes.data)
+        if rc != 0:
+            raise RuntimeError(f"scf_numeric failed with code {rc}")
+        return HostFactor(self.n, self.colptr.copy(), self.rowind.copy(), values, self.perm.copy())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _native.factor_lib().scf_free(h)
+            self._h = None
+
+
 @dataclasses.dataclass
 class FactoredSubdomain:
     """Library input for one subdomain: L in the fill-reducing order and B^T

@@ -2,7 +2,7 @@
  * every public header must compile as C, and the host-side entry points must
  * work from C without a GPU.  One subdomain: the 1D chain of n nodes, whose
  * factor L (tridiagonal lower) has the pattern {c, c+1} per column, glued at
- * two dofs. */
+ * two dofs; the host factor's two stages on the same chain's stiffness. */
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -83,6 +83,41 @@ int main(void) {
   CHECK(is.L_values == (int64_t)(2 * n - 1) && is.nnz_visited > 0 && is.flops == 4.0 * (double)is.nnz_visited,
         "implicit sizes");
   sci_destroy(ic);
+
+  /* host factor from C: the chain's stiffness (full symmetric CSC, node 0
+   * fixed), symbolic stage once, numeric stage into caller memory, equal to
+   * the one-call factorisation; then K -> 4 K gives L -> 2 L on free columns */
+  {
+    int64_t kcp[n + 1];
+    int32_t kri[3 * n - 2];
+    double kv[3 * n - 2], k4[3 * n - 2];
+    int64_t q = 0;
+    for (int c = 0; c < n; ++c) {
+      kcp[c] = q;
+      if (c > 0) { kri[q] = c - 1; kv[q++] = -1.0; }
+      kri[q] = c; kv[q++] = (c == 0 || c == n - 1) ? 1.0 : 2.0;
+      if (c + 1 < n) { kri[q] = c + 1; kv[q++] = -1.0; }
+    }
+    kcp[n] = q;
+    for (int64_t k = 0; k < q; ++k) k4[k] = 4.0 * kv[k];
+    const int32_t fixed0[1] = {0};
+    scf_factor *sym = NULL, *one = NULL;
+    CHECK(scf_analyze(n, kcp, kri, 1, fixed0, NULL, 0, &sym) == SCF_OK, "scf_analyze");
+    CHECK(scf_factorize(n, kcp, kri, kv, 1, fixed0, NULL, 0, &one) == SCF_OK, "scf_factorize");
+    const int64_t nnz = scf_nnz(sym);
+    CHECK(nnz == scf_nnz(one) && nnz == 2 * n - 2, "factor pattern size"); /* node 0: unit column */
+    double a[2 * n - 1], b[2 * n - 1], c4[2 * n - 1];
+    CHECK(scf_numeric(sym, kv, a) == SCF_OK && scf_numeric(sym, k4, c4) == SCF_OK, "scf_numeric");
+    CHECK(scf_export(one, NULL, NULL, b, NULL) == SCF_OK, "scf_export");
+    CHECK(memcmp(a, b, sizeof(double) * (size_t)nnz) == 0, "numeric stage differs from scf_factorize");
+    for (int64_t k = 1; k < nnz; ++k) CHECK(c4[k] == 2.0 * a[k], "K -> 4K must give L -> 2L");
+    CHECK(c4[0] == 1.0, "fixed dof keeps its unit column");
+    CHECK(scf_numeric(NULL, kv, a) == SCF_ERR_INVALID_ARG, "NULL handle accepted");
+    for (int64_t k = 0; k < q; ++k) k4[k] = -kv[k];
+    CHECK(scf_numeric(sym, k4, a) == SCF_ERR_NOT_SPD, "indefinite matrix accepted");
+    scf_free(sym);
+    scf_free(one);
+  }
 
   sc_mlp_shape shape = {10, 64, 8};
   CHECK(sc_mlp_param_count(&shape) == 64 * 10 + 64 + 64 * 64 + 64 + 8 * 64 + 8, "mlp parameter count");

@@ -389,6 +389,15 @@ def test_pipeline_create_validates_chunks():
     assert st == abi.SC_ERR_INVALID_ARG and "hi - lo" in msg
     st, msg = run([(0, 4), (2, nsub)], [p0, p1])
     assert st == abi.SC_ERR_INVALID_ARG
+    # the symbolic stage runs in scp_create: a subdomain whose ordering is not
+    # the one its plan was made for has another L pattern and is refused there
+    ident = np.arange(subs[2].n, dtype=np.int32)
+    keep.append(ident)
+    good_perm = subs[2].perm
+    subs[2].perm = ident.ctypes.data
+    st, msg = run([(0, 4), (4, nsub)], [p0, p1])
+    subs[2].perm = good_perm
+    assert st == abi.SC_ERR_INVALID_ARG and "subdomain 2" in msg and "the plan expects" in msg, msg
 
 
 def test_plan_rejects_bad_persistent_flag():
