@@ -587,7 +587,8 @@ def _split_section(args, fs, prob, Lv, lam, flush, stream, dev, fp64_ms):
 def run_config5(args):
     """Mixed batch: 1024 2D heat squares (edge 32..96) + 1024 3D elasticity cubes
     (edge 8..20), learned per-subdomain variant selection (autotuner on a third
-    of the subdomain classes as fallback and judge), workspace in waves."""
+    of the subdomain classes as fallback and as the yardstick of the learned choice),
+    workspace in waves."""
     import torch
 
     from paper_2509_21037_gb300 import host, sc, tune

@@ -17,7 +17,7 @@ error target.  This module
     features, and picks per subdomain the fastest variant predicted to meet
     the error target.  Classes the autotuner has measured keep its measured
     choice (the fallback); on the others the measured choice, when available,
-    is the judge of the learned choice's regret.
+    is the yardstick of the learned choice's regret.
 """
 from __future__ import annotations
 

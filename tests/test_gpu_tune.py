@@ -1,7 +1,7 @@
 """Autotuner and learned variant selector on a mixed 2D heat / 3D elasticity
 batch: the MLP, trained on the autotuner's records of half of the subdomain
 classes, picks variants for the other half; the autotuner's own measurements
-there judge its regret; the selected batch must beat the FP64-only batch and
+there measure its regret; the selected batch must beat the FP64-only batch and
 meet the error target."""
 import numpy as np
 import pytest
