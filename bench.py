@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 def _measured_hbm_gbps() -> float:
     """HBM copy bandwidth measured on this GPU model (MEASURED_PEAKS.json),
-    else the machine's fallback figure."""
+    else 6.8 TB/s, an earlier copy-bandwidth measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"])

@@ -20,7 +20,7 @@ correction touches only multipliers on fixed dofs and is applied as a sparse
 term after each `sc_apply`.
 
 Everything of the hot path (assembly, F * lambda) runs in the library's
-kernels; the driver's vector algebra (projections, dot products, the lumped
+kernels; the solver's vector algebra (projections, dot products, the lumped
 preconditioner sum_i B_i K_i B_i^T) is PyTorch on the device, and the set-up
 (G, e, d) and the recovery of the primal solution use host sparse triangular
 solves with the same factors.

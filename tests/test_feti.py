@@ -1,4 +1,4 @@
-"""CPU pins of the FETI-1 formulation that the PCPG driver (feti.py) runs on
+"""CPU pins of the FETI-1 formulation that the PCPG solver (feti.py) runs on
 the library's F: kernel bases, the fixed-dof correction of the generalised
 inverse, and a projected CG on the oracle's F that recovers a continuous,
 equilibrated primal solution."""

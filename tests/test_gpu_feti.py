@@ -1,4 +1,4 @@
-"""The FETI-1 PCPG driver (feti.py) on the library's assembled F: the dual
+"""The FETI-1 PCPG solver (feti.py) on the library's assembled F: the dual
 solution matches a projected CG on the oracle's operator, and the recovered
 primal solution is continuous across the interface and in equilibrium."""
 import numpy as np
