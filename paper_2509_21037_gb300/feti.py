@@ -19,18 +19,35 @@ and E_f the identity on them, so F = F_lib - sum_i B_i E_f,i B_i^T: the
 correction touches only multipliers on fixed dofs and is applied as a sparse
 term after each `sc_apply`.
 
+Preconditioners (approximations of F^{-1}): lumped, W (sum_i B_i K_i B_i^T) W
+(a sparse product on the device), and Dirichlet, W (sum_i B_i S_i B_i^T) W
+with S_i the Schur complement of K_i onto the dofs its multipliers glue (the
+other dofs, K_i's interior, eliminated).  W = (B B^T)^+ is the scaling
+that makes them consistent for any B (the inverse for a full-row-rank B, the
+pseudo-inverse where multipliers are redundant): with the non-redundant
+gluing here (a node shared by q subdomains carries q - 1 multipliers per dof)
+the unscaled sums weight edge and corner multipliers wrongly and take more
+iterations than no preconditioner at all.  B B^T couples only the
+multipliers of one dof, so W is block diagonal with blocks of at most 7.
+The Dirichlet blocks B_i S_i B_i^T are m_i x m_i, in F_i's local multiplier
+order, so they are tile-packed into the plan's F layout and applied by the
+library's own `sc_apply`, like F.
+
 Everything of the hot path (assembly, F * lambda) runs in the library's
 kernels; the solver's vector algebra (projections, dot products, the lumped
-preconditioner sum_i B_i K_i B_i^T) is PyTorch on the device, and the set-up
-(G, e, d) and the recovery of the primal solution use host sparse triangular
-solves with the same factors.
+preconditioner) is PyTorch on the device, and the set-up (G, e, d, the
+Dirichlet Schur complements) and the recovery of the primal solution run on
+the host (sparse triangular solves with the same factors; dense LAPACK
+Cholesky of each distinct interior block).
 """
 from __future__ import annotations
 
 import dataclasses
+import time
 from typing import List, Optional, Sequence
 
 import numpy as np
+import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
@@ -56,6 +73,78 @@ def kernel_basis(sd) -> np.ndarray:
     R[1::3, 4], R[2::3, 4] = -z, y          # rotation about x
     R[0::3, 5], R[2::3, 5] = z, -x          # rotation about y
     return R
+
+
+def bbt_inverse(subdomains, n_dual: int) -> sp.csr_matrix:
+    """W = (B B^T)^+ for the global gluing B (the inverse where B has full
+    row rank, as with non-redundant gluing; the pseudo-inverse where
+    multipliers close a loop): B B^T = sum_i B_i B_i^T scattered by the
+    lambda maps, inverted block by block over the connected components of
+    its graph (the multipliers sharing one dof), components of equal size
+    together in one batched dense pseudo-inverse."""
+    from scipy.sparse import csgraph
+    rows, cols, vals = [], [], []
+    for sd in subdomains:
+        lm = np.asarray(sd.lambda_map, np.int64)
+        Bt = sp.csc_matrix(sd.Bt)
+        C = (Bt.T @ Bt).tocoo()
+        rows.append(lm[C.row]); cols.append(lm[C.col]); vals.append(C.data)
+    BB = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n_dual, n_dual))
+    ncomp, label = csgraph.connected_components(BB, directed=False)
+    order = np.argsort(label, kind="stable")
+    start = np.searchsorted(label[order], np.arange(ncomp + 1))
+    size = np.diff(start)
+    r, c, v = [], [], []
+    for k in np.unique(size):
+        comps = np.nonzero(size == k)[0]
+        idx = order[start[comps][:, None] + np.arange(k)[None, :]]          # (ncomp_k, k)
+        rr = np.repeat(idx, k, axis=1).ravel()
+        cc = np.tile(idx, (1, k)).ravel()
+        blocks = np.asarray(BB[rr, cc]).reshape(len(comps), k, k)
+        r.append(rr); c.append(cc); v.append(np.linalg.pinv(blocks, rcond=1e-12, hermitian=True).ravel())
+    return sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(n_dual, n_dual))
+
+
+def glued_dofs(sd) -> np.ndarray:
+    """The dofs of a subdomain that its multipliers touch (rows of B_i^T
+    holding a nonzero), ascending."""
+    Bt = sp.csc_matrix(sd.Bt)
+    return np.unique(Bt.indices[Bt.data != 0])
+
+
+def schur_on_glued(sd) -> np.ndarray:
+    """S_i = K_bb - K_bi K_ii^{-1} K_ib on the glued dofs b (``glued_dofs``),
+    i the other dofs: dense Cholesky K_ii = C C^T, X = C^{-1} K_ib,
+    S = K_bb - X^T X.  K_ii is nonsingular whenever the glued dofs meet every
+    rigid-body mode (a subdomain glued along a whole face); otherwise the
+    Cholesky raises numpy.linalg.LinAlgError."""
+    K = sp.csr_matrix(sd.K)
+    n = K.shape[0]
+    b = glued_dofs(sd)
+    if len(b) == 0:
+        return np.zeros((0, 0))
+    i = np.setdiff1d(np.arange(n), b)
+    Kbb = K[b][:, b].toarray()
+    if len(i) == 0:
+        return Kbb
+    Kii = K[i][:, i].toarray()
+    Kib = K[i][:, b].toarray()
+    C = sla.cholesky(Kii, lower=True)
+    X = sla.solve_triangular(C, Kib, lower=True)
+    S = Kbb - X.T @ X
+    return 0.5 * (S + S.T)
+
+
+def dirichlet_block(sd, S: Optional[np.ndarray] = None) -> np.ndarray:
+    """B_i S_i B_i^T restricted to the subdomain's multipliers: the m_i x m_i
+    block of the Dirichlet preconditioner, in F_i's local multiplier order."""
+    if S is None:
+        S = schur_on_glued(sd)
+    Bt = sp.csc_matrix(sd.Bt)
+    Bb = Bt[glued_dofs(sd)]                      # |b| x m, the signed-Boolean rows that glue
+    W = np.asarray(Bb.T @ S)                     # Bb^T S, m x |b|
+    P = np.asarray(Bb.T @ W.T)                   # Bb^T (Bb^T S)^T = Bb^T S Bb (S symmetric)
+    return 0.5 * (P + P.T)
 
 
 class _KPlus:
@@ -94,12 +183,20 @@ class FETIResult:
 class FETISolver:
     """PCPG on the dual interface problem with the assembled F on the GPU.
 
-    precond: "lumped" (sum_i B_i K_i B_i^T) or "none".
+    precond: "lumped" (sum_i B_i K_i B_i^T), "dirichlet" (sum_i B_i S_i B_i^T,
+    applied with the library's sc_apply on a tile-packed copy) or "none";
+    scaling: "bbt" (W M W, W = (B B^T)^+) or "none" (M alone).
+    ``precond_setup_s`` is the host time of the Dirichlet Schur complements
+    (one per distinct (K_i, glued dofs) pair).
     """
 
     def __init__(self, problem, factored: Optional[Sequence] = None, device="cuda", precond: str = "lumped",
-                 plan_kwargs: Optional[dict] = None):
+                 plan_kwargs: Optional[dict] = None, scaling: str = "bbt"):
         import torch
+        if precond not in ("lumped", "dirichlet", "none"):
+            raise ValueError(f"unknown preconditioner {precond!r}")
+        if scaling not in ("bbt", "none"):
+            raise ValueError(f"unknown scaling {scaling!r}")
         self.torch = torch
         self.dev = torch.device(device)
         subs = problem.subdomains
@@ -136,6 +233,25 @@ class FETISolver:
         self.C = self._sparse(np.concatenate(crow), np.concatenate(ccol), np.concatenate(cval))
         self.M = self._sparse(*_coo(M)) if precond == "lumped" else None
         self.q = torch.empty(self.nd, dtype=torch.float64, device=self.dev)
+        self.Mdir, self.precond_setup_s = None, 0.0
+        if precond == "dirichlet":
+            t0 = time.perf_counter()
+            cache = {}
+            blocks = []
+            for sd in subs:
+                key = None if sd.key is None else (sd.key, glued_dofs(sd).tobytes())
+                S = cache.get(key) if key is not None else None
+                if S is None:
+                    S = schur_on_glued(sd)
+                    if key is not None:
+                        cache[key] = S
+                blocks.append(dirichlet_block(sd, S))
+            self.precond_setup_s = time.perf_counter() - t0
+            self.Mdir = self.plan.pack(blocks, self.dev)
+            self.qz = torch.empty(self.nd, dtype=torch.float64, device=self.dev)
+        self.W = None
+        if precond != "none" and scaling == "bbt":
+            self.W = self._sparse(*_coo(bbt_inverse(subs, self.nd)))
 
     def _sparse(self, r, c, v):
         t = self.torch
@@ -149,6 +265,22 @@ class FETISolver:
 
     def project(self, x):
         return x - self.G @ (self.GtG_pinv @ (self.G.T @ x))
+
+    def precondition(self, w):
+        """z = P W M W w for the chosen preconditioner M and scaling W
+        (w itself without a preconditioner)."""
+        t = self.torch
+        if self.M is None and self.Mdir is None:
+            return w
+        x = w if self.W is None else t.sparse.mm(self.W, w[:, None])[:, 0]
+        if self.M is not None:
+            y = t.sparse.mm(self.M, x[:, None])[:, 0]
+        else:
+            self.plan.apply(self.Mdir, x.contiguous(), self.qz)
+            y = self.qz
+        if self.W is not None:
+            y = t.sparse.mm(self.W, y[:, None])[:, 0]
+        return self.project(y)
 
     def solve(self, loads: Sequence[np.ndarray], tol: float = 1e-10, maxit: int = 1000) -> FETIResult:
         t = self.torch
@@ -170,7 +302,7 @@ class FETISolver:
         res, p, zw_old, it = [1.0], None, None, 0
         if w0 > 0:
             for it in range(1, maxit + 1):
-                z = self.project(t.sparse.mm(self.M, w[:, None])[:, 0]) if self.M is not None else w
+                z = self.precondition(w)
                 zw = t.dot(z, w)
                 p = z if p is None else z + (zw / zw_old) * p
                 qv = self.apply_F(p)

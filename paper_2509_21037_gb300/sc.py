@@ -132,6 +132,31 @@ class Plan:
         self._check(self.lib.sc_export_F(self.h, F.data_ptr(), i, dst.data_ptr(), max(1, m), _stream_ptr(stream)))
         return dst.t()
 
+    def pack(self, mats: Sequence, device="cuda"):
+        """The inverse of ``export``: dense symmetric m_i x m_i matrices, in
+        each subdomain's local multiplier order, tile-packed into a buffer of
+        this plan's F layout (lower 32x32 tiles, diagonal tiles full, padding
+        zero), so that ``apply`` runs any operator of F's shape, e.g. a
+        preconditioner sum_i B_i M_i B_i^T."""
+        import torch
+        assert len(mats) == self.nsub
+        buf = torch.zeros(max(1, self.sizes.F_doubles), dtype=torch.float64, device=device)
+        for i, M in enumerate(mats):
+            m = self.m[i]
+            nt = (m + 31) // 32
+            if nt == 0:
+                continue
+            A = torch.zeros((nt * 32, nt * 32), dtype=torch.float64, device=device)
+            A[:m, :m] = torch.as_tensor(np.asarray(M, dtype=np.float64), device=device)
+            # tiles[I, J, c, r] = A[32 I + r, 32 J + c]; tile (I, J) is number I (I + 1) / 2 + J
+            T = A.reshape(nt, 32, nt, 32).permute(0, 2, 3, 1)
+            I, J = torch.tril_indices(nt, nt, device=device)
+            tiles = T[I, J].reshape(-1)
+            off = int(self.F_offsets[i])
+            assert int(self.F_offsets[i + 1]) - off == tiles.numel()
+            buf[off:off + tiles.numel()] = tiles
+        return buf
+
     def enable_stage_timing(self, on: bool = True):
         self._check(self.lib.sc_enable_stage_timing(self.h, int(on)))
 

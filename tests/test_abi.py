@@ -418,3 +418,35 @@ def test_plan_rejects_bad_persistent_flag():
         assert (st == abi.SC_OK) == ok, (flag, st, msg)
         if not ok:
             assert "persistent" in msg
+
+
+def test_pack_is_the_inverse_of_export():
+    """Plan.pack writes dense symmetric m_i x m_i matrices into the plan's F
+    layout: tile (I, J), J <= I, at I (I + 1) / 2 + J, entry (r, c) of a tile
+    at r + 32 c, diagonal tiles full, padding zero; the plan replay's export
+    reads them back unchanged."""
+    torch = pytest.importorskip("torch")
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    plan = sc.Plan(fs, prob.n_dual)
+    assert any(m % 32 for m in plan.m) and max(plan.m) > 32
+    rng = np.random.default_rng(11)
+    mats = []
+    for m in plan.m:
+        A = rng.standard_normal((m, m))
+        mats.append(A + A.T)
+    buf = plan.pack(mats, device="cpu").numpy()
+    assert buf.shape == (max(1, plan.sizes.F_doubles),)
+    T = pe.export_plan(plan)
+    for i, M in enumerate(mats):
+        m = plan.m[i]
+        nt = (m + 31) // 32
+        off = int(plan.F_offsets[i])
+        for I in range(nt):
+            for J in range(I + 1):
+                tile = buf[off + (I * (I + 1) // 2 + J) * 1024:][:1024].reshape(32, 32)   # [c, r]
+                want = np.zeros((32, 32))
+                rows, cols = min(32, m - 32 * I), min(32, m - 32 * J)
+                want[:cols, :rows] = M[32 * I:32 * I + rows, 32 * J:32 * J + cols].T
+                assert np.array_equal(tile, want)
+        assert np.array_equal(pe.export_dense(T, buf, i), M)

@@ -92,3 +92,98 @@ def test_projected_cg_on_oracle_operator_solves_the_decomposed_problem():
         jump[lm] += Bt.T @ u
         us.append(u)
     assert np.linalg.norm(jump) <= 1e-9 * max(np.linalg.norm(u) for u in us)        # continuity
+
+
+def test_schur_on_glued_dofs():
+    """S_i (feti.schur_on_glued) against its definition through the harmonic
+    extension, solved independently with a sparse LU: S u_b = K_bb u_b +
+    K_bi u_i with K_ii u_i = -K_ib u_b; S annihilates the rigid-body modes
+    restricted to the glued dofs and is positive semidefinite."""
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(2)
+    for prob in (synth.cube_heat_3d(2, 4, coef_seed=1), synth.elasticity_cubes((2, 1, 1), 3, 3, seed=0)):
+        for sd in prob.subdomains[:2]:
+            S = feti.schur_on_glued(sd)
+            b = feti.glued_dofs(sd)
+            K = sp.csr_matrix(sd.K)
+            i = np.setdiff1d(np.arange(K.shape[0]), b)
+            lu = spla.splu(sp.csc_matrix(K[i][:, i]))
+            for _ in range(3):
+                ub = rng.standard_normal(len(b))
+                ui = lu.solve(-(K[i][:, b] @ ub))
+                ref = K[b][:, b] @ ub + K[b][:, i] @ ui
+                assert np.linalg.norm(S @ ub - ref) <= 1e-10 * np.linalg.norm(ref)
+            R = feti.kernel_basis(sd)[b]
+            assert np.abs(S @ R).max() <= 1e-9 * np.abs(S).max() * np.abs(R).max()
+            assert np.linalg.eigvalsh(S).min() >= -1e-10 * np.abs(S).max()
+
+
+def _pcpg(F, G, d, e, precond=None, tol=1e-10, maxit=500):
+    GtGp = np.linalg.pinv(G.T @ G, rcond=1e-12, hermitian=True)
+    P = lambda x: x - G @ (GtGp @ (G.T @ x))
+    lam = G @ (GtGp @ e)
+    r = d - F @ lam
+    w = P(r)
+    w0 = np.linalg.norm(w)
+    p, zw_old = None, None
+    for it in range(1, maxit + 1):
+        z = w if precond is None else P(precond @ w)
+        zw = z @ w
+        p = z if p is None else z + zw / zw_old * p
+        q = F @ p
+        eta = zw / (p @ q)
+        lam, r = lam + eta * p, r - eta * q
+        w, zw_old = P(r), zw
+        if np.linalg.norm(w) < tol * w0:
+            return lam, it
+    raise AssertionError("PCPG did not converge")
+
+
+def _bbt(prob):
+    nd = prob.n_dual
+    BB = np.zeros((nd, nd))
+    for sd in prob.subdomains:
+        lm = np.asarray(sd.lambda_map)
+        Bt = sd.Bt.toarray()
+        BB[np.ix_(lm, lm)] += Bt.T @ Bt
+    return BB
+
+
+def test_bbt_inverse_is_the_pseudo_inverse():
+    """feti.bbt_inverse against numpy's dense pseudo-inverse of B B^T: heat
+    (non-redundant gluing, B B^T invertible) and an elasticity lattice whose
+    multipliers close loops (B B^T singular)."""
+    for prob in (synth.cube_heat_3d(3, 3), synth.elasticity_cubes((2, 2, 1), 3, 3, seed=0)):
+        BB = _bbt(prob)
+        W = feti.bbt_inverse(prob.subdomains, prob.n_dual).toarray()
+        assert np.abs(W - np.linalg.pinv(BB, hermitian=True)).max() <= 1e-13
+    assert np.linalg.matrix_rank(_bbt(synth.elasticity_cubes((2, 2, 1), 3, 3, seed=0))) < 192
+
+
+def test_scaled_preconditioners_cut_iterations():
+    """PCPG on the oracle's operator with the Dirichlet preconditioner
+    W (sum_i B_i S_i B_i^T) W (blocks from feti.dirichlet_block, scattered by
+    the lambda maps) and the lumped W (sum_i B_i K_i B_i^T) W, W = (B B^T)^+
+    computed here densely: both converge to the multipliers of the
+    unpreconditioned solve, Dirichlet in the fewest iterations; without W the
+    same sums take more iterations than no preconditioner (the non-redundant
+    gluing weights edge and corner multipliers wrongly)."""
+    prob = synth.cube_heat_3d(3, 4, coef_seed=3)
+    loads = feti.compatible_loads(prob, seed=5)
+    F, G, d, e = _dual_problem(prob, loads)
+    nd = prob.n_dual
+    MD = np.zeros((nd, nd))
+    ML = np.zeros((nd, nd))
+    for sd in prob.subdomains:
+        lm = np.asarray(sd.lambda_map)
+        Bt = sd.Bt.toarray()
+        MD[np.ix_(lm, lm)] += feti.dirichlet_block(sd)
+        ML[np.ix_(lm, lm)] += Bt.T @ sd.K.toarray() @ Bt
+    W = np.linalg.pinv(_bbt(prob), hermitian=True)
+    lam0, n0 = _pcpg(F, G, d, e)
+    lamL, nL = _pcpg(F, G, d, e, W @ ML @ W)
+    lamD, nD = _pcpg(F, G, d, e, W @ MD @ W)
+    for lam in (lamL, lamD):
+        assert np.linalg.norm(lam - lam0) <= 1e-7 * np.linalg.norm(lam0)
+    assert nD < nL < n0 // 3, (nD, nL, n0)
+    assert _pcpg(F, G, d, e, ML)[1] > n0 and _pcpg(F, G, d, e, MD)[1] > n0
