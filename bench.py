@@ -255,12 +255,15 @@ def _feti_section(prob, fs, dev, t_asm, t_expl, t_gimpl, t_himpl):
     projected residual with the Dirichlet and lumped preconditioners (both
     scaled by (B B^T)^+) and without one, and what a solve of that many
     iterations costs with the explicit operator (assembly + applications)
-    against the GPU and host implicit applications."""
+    against the GPU and host implicit applications.  Each solver solves once
+    untimed first: the first solve after set-up also pays the first use of
+    the loop's device kernels (seconds once, against ~20-50 ms a solve)."""
     from paper_2509_21037_gb300 import feti
     loads = feti.compatible_loads(prob, seed=1)
     out = {}
     for pc in ("dirichlet", "lumped", "none"):
         solver = feti.FETISolver(prob, fs, device=dev, precond=pc)
+        solver.solve(loads, tol=1e-10)
         res = solver.solve(loads, tol=1e-10)
         n = res.iterations
         out[pc] = {"iterations": n, "pcpg_ms": res.solve_ms, "F_apply_ms": res.apply_ms,
