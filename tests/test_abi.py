@@ -450,3 +450,45 @@ def test_pack_is_the_inverse_of_export():
                 want[:cols, :rows] = M[32 * I:32 * I + rows, 32 * J:32 * J + cols].T
                 assert np.array_equal(tile, want)
         assert np.array_equal(pe.export_dense(T, buf, i), M)
+
+
+@pytest.mark.parametrize("name,prob", list(_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_plan_predicts_the_structure_of_Y(name, prob):
+    """Structural pins on Y = L^{-1} P B^T (paper Sec. 3.2): computed here
+    with a plain sparse triangular solve (scipy), independent of the plan,
+    every nonzero of Y lies where the plan keeps Y (rows of a supernode s,
+    sorted columns [jlo_s, jhi_s), and within the column cut of the row's
+    32-row block); Y(r, j) = 0 above the pivot p_j (sorted columns, so the
+    pruning by pivots is never lossy); and the pivots are non-decreasing in
+    the sorted order."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    fs = host.factorize_problem(prob.subdomains)
+    plan = sc.Plan(fs, prob.n_dual)
+    T = pe.export_plan(plan)
+    sns = T["sns"]
+    kept_total = nnz_total = 0
+    for i, f in enumerate(fs):
+        sd = T["subs"][i]
+        n, m = f.n, f.m
+        if m == 0:
+            continue
+        L = sp.csc_matrix((f.L.values, f.L.rowind, f.L.colptr), shape=(n, n))
+        Bt = sp.csc_matrix((f.bt_sign.astype(float), f.bt_rowind, f.bt_colptr), shape=(n, m))
+        perm = T["perm"][sd["col_off"]:sd["col_off"] + m]
+        Bs = Bt[:, perm]
+        piv = np.array([Bs.indices[Bs.indptr[j]:Bs.indptr[j + 1]].min() for j in range(m)])
+        assert np.all(np.diff(piv) >= 0)
+        Y = spla.spsolve_triangular(L.tocsr(), Bs.toarray(), lower=True)
+        nz = Y != 0.0
+        assert not np.any(nz & (np.arange(n)[:, None] < piv[None, :])), "Y nonzero above a pivot"
+        kept = np.zeros((n, m), bool)
+        for s in sns[sns["sub"] == i]:
+            for kb in range(0, s["ns"], 32):
+                cut = min(int(s["jhi"]), int(T["cuts"][s["cut_off"] + kb // 32]))
+                r0 = s["c0"] + kb
+                kept[r0:r0 + min(32, s["ns"] - kb), s["jlo"]:cut] = True
+        assert not np.any(nz & ~kept), f"subdomain {i}: Y nonzero where the plan keeps none"
+        kept_total += kept.sum()
+        nnz_total += nz.sum()
+    assert nnz_total > 0 and kept_total >= nnz_total
