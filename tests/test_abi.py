@@ -7,6 +7,7 @@ import re
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import oracle
 import synth
@@ -132,8 +133,22 @@ def test_empty_batch_and_empty_subdomain():
     assert st == abi.SC_OK, msg
 
 
+def edge_batch():
+    """cube_heat_3d(2, 5) with subdomain 0 unglued (m = 0) and subdomains 1,
+    2, 3 cut to 64, 32 and 1 multipliers (exact tile multiples and a single
+    column); the others keep their ragged 91..102."""
+    prob = synth.cube_heat_3d(2, 5)
+    subs = list(prob.subdomains)
+    for i, m in ((0, 0), (1, 64), (2, 32), (3, 1)):
+        sd = subs[i]
+        subs[i] = synth.Subdomain(K=sd.K, fixed=sd.fixed, Bt=sp.csc_matrix(sd.Bt)[:, :m],
+                                  lambda_map=np.asarray(sd.lambda_map)[:m], grid=sd.grid, ndpn=sd.ndpn, key=None)
+    return synth.Problem(name="edge_batch", subdomains=subs, n_dual=prob.n_dual, seed=0, description="edge cases")
+
+
 def _cases():
     yield "config1", synth.make_config(1)
+    yield "edge_batch", edge_batch()
     yield "cube_2x5", synth.cube_heat_3d(2, 5)
     yield "cube_coef", synth.cube_heat_3d(2, 3, coef_seed=4)
     yield "elast", synth.elasticity_cubes((2, 1, 1), 2, 3, seed=1)
