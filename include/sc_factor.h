@@ -89,6 +89,25 @@ typedef struct {
 int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, const double *lambda,
                        double *q, int32_t nthreads);
 
+/* The same product with its symbolic work done once (the implicit approach's
+ * own preprocessing, paper Sec. 2.2).  scf_implicit_plan reads the patterns:
+ * per subdomain the supernodes of L (runs of columns with one shared
+ * pattern, checked entry by entry) and the supernodes on the etree paths from
+ * B^T's rows, the only ones the two solves touch.  It copies the
+ * scf_apply_subdomain records but not the arrays they point to: those must
+ * stay valid, and their patterns unchanged, while the plan is used; L's
+ * values may change between runs (new factor, same pattern).
+ * scf_implicit_run then solves supernode by supernode: dense triangles on
+ * contiguous rows, the rows below updated from contiguous L values through
+ * one scatter (forward) or one gather (backward) per supernode.  Same
+ * threading and fixed summation order as scf_implicit_apply; the results of
+ * the two agree to rounding.  SCF_ERR_INVALID_ARG on bad sizes, maps or row
+ * indices; SCF_ERR_OOM if the plan cannot be allocated (*out stays NULL). */
+typedef struct scf_implicit scf_implicit;
+int scf_implicit_plan(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, scf_implicit **out);
+int scf_implicit_run(const scf_implicit *plan, const double *lambda, double *q, int32_t nthreads);
+void scf_implicit_free(scf_implicit *plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,12 @@ def factor_lib() -> ctypes.CDLL:
         lib.scf_free.restype = None
         lib.scf_implicit_apply.argtypes = [c_i32, c_vp, c_i64, c_vp, c_vp, c_i32]
         lib.scf_implicit_apply.restype = c_int
+        lib.scf_implicit_plan.argtypes = [c_i32, c_vp, c_i64, ctypes.POINTER(c_vp)]
+        lib.scf_implicit_plan.restype = c_int
+        lib.scf_implicit_run.argtypes = [c_vp, c_vp, c_vp, c_i32]
+        lib.scf_implicit_run.restype = c_int
+        lib.scf_implicit_free.argtypes = [c_vp]
+        lib.scf_implicit_free.restype = None
         lib._typed = True
     return lib
 

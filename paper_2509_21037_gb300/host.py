@@ -208,9 +208,11 @@ class _ApplySub(ctypes.Structure):
 class ImplicitApply:
     """Host implicit application q = sum_i B_i L_i^-T L_i^-1 B_i^T lambda_i
     (paper Eq. "dualop_apply_impl"), the per-iteration alternative to the
-    explicit F*lambda."""
+    explicit F*lambda.  planned=True (default) makes the supernodal plan once
+    (scf_implicit_plan) and runs it per call (scf_implicit_run);
+    planned=False runs the column-by-column scf_implicit_apply."""
 
-    def __init__(self, subdomains: Sequence[FactoredSubdomain], n_dual: int):
+    def __init__(self, subdomains: Sequence[FactoredSubdomain], n_dual: int, planned: bool = True):
         self.lib = _native.factor_lib()
         self.n_dual = int(n_dual)
         self._keep = []
@@ -226,14 +228,31 @@ class ImplicitApply:
             s.L_colptr, s.L_rowind, s.L_val, s.Bt_colptr, s.Bt_rowind, s.Bt_sign, s.lambda_map = \
                 [x.ctypes.data if x.size else None for x in a]
         self.nsub = len(subdomains)
+        self._plan = None
+        if planned:
+            h = ctypes.c_void_p()
+            rc = self.lib.scf_implicit_plan(self.nsub, self.arr, self.n_dual, ctypes.byref(h))
+            if rc != 0:
+                raise RuntimeError(f"scf_implicit_plan failed ({rc})")
+            self._plan = h
 
     def __call__(self, lam: np.ndarray, threads: int = 0) -> np.ndarray:
         lam = np.ascontiguousarray(lam, np.float64)
         q = np.empty(self.n_dual)
-        rc = self.lib.scf_implicit_apply(self.nsub, self.arr, self.n_dual, lam.ctypes.data, q.ctypes.data, threads)
+        if self._plan is not None:
+            rc = self.lib.scf_implicit_run(self._plan, lam.ctypes.data, q.ctypes.data, threads)
+        else:
+            rc = self.lib.scf_implicit_apply(self.nsub, self.arr, self.n_dual, lam.ctypes.data, q.ctypes.data,
+                                             threads)
         if rc != 0:
-            raise RuntimeError(f"scf_implicit_apply failed ({rc})")
+            raise RuntimeError(f"host implicit apply failed ({rc})")
         return q
+
+    def __del__(self):
+        h = getattr(self, "_plan", None)
+        if h is not None and h.value:
+            self.lib.scf_implicit_free(h)
+            self._plan = None
 
 
 def factorize_problem(subdomains, threads: int = 0, leaf: int = 8) -> List[FactoredSubdomain]:

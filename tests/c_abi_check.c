@@ -3,6 +3,7 @@
  * work from C without a GPU.  One subdomain: the 1D chain of n nodes, whose
  * factor L (tridiagonal lower) has the pattern {c, c+1} per column, glued at
  * two dofs; the host factor's two stages on the same chain's stiffness. */
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -115,6 +116,34 @@ int main(void) {
     CHECK(scf_numeric(NULL, kv, a) == SCF_ERR_INVALID_ARG, "NULL handle accepted");
     for (int64_t k = 0; k < q; ++k) k4[k] = -kv[k];
     CHECK(scf_numeric(sym, k4, a) == SCF_ERR_NOT_SPD, "indefinite matrix accepted");
+    /* host implicit apply from C: planned and column by column agree */
+    {
+      double lv[2 * n - 1];
+      CHECK(scf_numeric(sym, kv, lv) == SCF_OK, "scf_numeric for the implicit apply");
+      int64_t lcp[n + 1];
+      int32_t lri[2 * n - 1];
+      CHECK(scf_export(sym, lcp, lri, NULL, NULL) == SCF_OK, "scf_export pattern");
+      scf_apply_subdomain as;
+      memset(&as, 0, sizeof as);
+      as.n = n;
+      as.m = m;
+      as.L_colptr = lcp;
+      as.L_rowind = lri;
+      as.L_val = lv;
+      as.Bt_colptr = bt_colptr;
+      as.Bt_rowind = bt_rowind;
+      as.Bt_sign = bt_sign;
+      as.lambda_map = lambda_map;
+      const double lam[m] = {0.75, -1.5};
+      double q1[m], q2[m];
+      scf_implicit *ip = NULL;
+      CHECK(scf_implicit_apply(1, &as, m, lam, q1, 1) == SCF_OK, "scf_implicit_apply");
+      CHECK(scf_implicit_plan(1, &as, m, &ip) == SCF_OK && ip, "scf_implicit_plan");
+      CHECK(scf_implicit_run(ip, lam, q2, 1) == SCF_OK, "scf_implicit_run");
+      for (int j = 0; j < m; ++j) CHECK(fabs(q1[j] - q2[j]) <= 1e-14 * (fabs(q1[j]) + 1.0), "planned apply differs");
+      CHECK(scf_implicit_run(NULL, lam, q2, 1) == SCF_ERR_INVALID_ARG, "NULL plan accepted");
+      scf_implicit_free(ip);
+    }
     scf_free(sym);
     scf_free(one);
   }

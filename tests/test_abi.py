@@ -229,15 +229,47 @@ def test_perfect_triangle_emulation():
     assert oracle.relative_frobenius(F, ref) < 1e-12
 
 
+@pytest.mark.parametrize("planned", [True, False])
 @pytest.mark.parametrize("threads", [1, 3])
-def test_host_implicit_apply_matches_oracle(threads):
-    prob = synth.cube_heat_3d(2, 4, coef_seed=2)
-    fs = host.factorize_problem(prob.subdomains)
-    lam = np.random.default_rng(9).standard_normal(prob.n_dual)
-    q = host.ImplicitApply(fs, prob.n_dual)(lam, threads=threads)
-    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains), [s.lambda_map for s in prob.subdomains],
-                           lam, prob.n_dual)
-    assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+def test_host_implicit_apply_matches_oracle(threads, planned):
+    for prob in (synth.cube_heat_3d(2, 4, coef_seed=2), edge_batch(), synth.elasticity_cubes((2, 1, 1), 2, 4, seed=1)):
+        fs = host.factorize_problem(prob.subdomains)
+        lam = np.random.default_rng(9).standard_normal(prob.n_dual)
+        q = host.ImplicitApply(fs, prob.n_dual, planned=planned)(lam, threads=threads)
+        Fo = [oracle.dual_operator(sd, refine=1) if sd.m else np.zeros((0, 0)) for sd in prob.subdomains]
+        qo = oracle.apply_dual(Fo, [s.lambda_map for s in prob.subdomains], lam, prob.n_dual)
+        assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+
+
+def test_host_implicit_plan_checks_patterns_entry_by_entry():
+    """A lower-triangular L whose neighbouring columns have matching counts
+    and parents but different rows must not be merged into one supernode: the
+    planned apply equals the column-by-column one (and a dense solve) on it,
+    with several nonzeros per B^T column and an empty one."""
+    rng = np.random.default_rng(5)
+    n = 12
+    cols = {0: [0, 1, 3, 7], 1: [1, 2, 5], 2: [2, 5, 9], 3: [3, 4], 4: [4, 6], 5: [5, 9, 11], 6: [6, 7],
+            7: [7, 8], 8: [8, 10], 9: [9, 11], 10: [10, 11], 11: [11]}
+    colptr = np.zeros(n + 1, np.int64)
+    rowind, vals = [], []
+    for c in range(n):
+        rows = cols[c]
+        rowind += rows
+        vals += [3.0 + rng.uniform()] + list(rng.uniform(-0.5, 0.5, len(rows) - 1))
+        colptr[c + 1] = len(rowind)
+    L = host.HostFactor(n, colptr, np.array(rowind, np.int32), np.array(vals), np.arange(n, dtype=np.int32))
+    Bt = sp.csc_matrix(([1.0, -1.0, 1.0, 1.0, -1.0], ([0, 4, 8, 11, 2], [0, 0, 1, 2, 3])), shape=(n, 5))
+    fsd = host.FactoredSubdomain(L=L, bt_colptr=Bt.indptr.astype(np.int32), bt_rowind=Bt.indices.astype(np.int32),
+                                 bt_sign=Bt.data.astype(np.int8), lambda_map=np.array([4, 0, 2, 1, 3], np.int32))
+    lam = rng.standard_normal(5)
+    qp = host.ImplicitApply([fsd], 5, planned=True)(lam, threads=1)
+    qc = host.ImplicitApply([fsd], 5, planned=False)(lam, threads=1)
+    Ld = sp.csc_matrix((L.values, L.rowind, L.colptr), shape=(n, n)).toarray()
+    Bd = Bt.toarray()
+    Fd = Bd.T @ np.linalg.solve(Ld.T, np.linalg.solve(Ld, Bd))
+    qd = np.zeros(5)
+    np.add.at(qd, fsd.lambda_map, Fd @ lam[fsd.lambda_map])
+    assert np.allclose(qp, qd, rtol=1e-13, atol=1e-13) and np.allclose(qc, qd, rtol=1e-13, atol=1e-13)
 
 
 def test_mlp_header_symbols_exported():

@@ -23,7 +23,7 @@ def test_c_client_of_the_abi(tmp_path):
     cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
            os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L", lib, "-lsc", "-lscfactor",
            "-Wl,-rpath," + lib, "-L", os.path.join(cuda, "lib64"), "-Wl,-rpath," + os.path.join(cuda, "lib64"),
-           "-lcudart"]
+           "-lcudart", "-lm"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
