@@ -157,10 +157,13 @@ class SymbolicFactor:
         return HostFactor(self.n, self.colptr.copy(), self.rowind.copy(), values, self.perm.copy())
 
     def __del__(self):
-        h = getattr(self, "_h", None)
-        if h:
-            _native.factor_lib().scf_free(h)
-            self._h = None
+        try:
+            h = getattr(self, "_h", None)
+            if h is not None and h.value:
+                _native.factor_lib().scf_free(h)
+                self._h = None
+        except Exception:
+            pass
 
 
 @dataclasses.dataclass
@@ -249,10 +252,13 @@ class ImplicitApply:
         return q
 
     def __del__(self):
-        h = getattr(self, "_plan", None)
-        if h is not None and h.value:
-            self.lib.scf_implicit_free(h)
-            self._plan = None
+        try:
+            h = getattr(self, "_plan", None)
+            if h is not None and h.value:
+                self.lib.scf_implicit_free(h)
+                self._plan = None
+        except Exception:
+            pass
 
 
 def factorize_problem(subdomains, threads: int = 0, leaf: int = 8) -> List[FactoredSubdomain]:
