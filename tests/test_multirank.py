@@ -59,3 +59,20 @@ def test_max_over_ranks_and_rank0_only_reference():
     assert maxes == [15.0, 15.0]
     ref = [v for k, r, v in got if k == "ref"]
     assert ref == [(0, "")]
+
+
+def test_unmemoised_oracle_cost_covers_every_size():
+    """bench's un-memoised oracle figure: one fresh-memo oracle run per
+    distinct subdomain size, projected over the batch by the size counts."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    prob = synth.elasticity_cubes((3, 1, 1), 2, 3, seed=2)       # sizes 81, 81, 192
+    sizes = {}
+    for sd in prob.subdomains:
+        sizes[sd.K.shape[0]] = sizes.get(sd.K.shape[0], 0) + 1
+    out = bench._oracle_unmemoised(prob)
+    per = out["s_per_subdomain"]
+    assert set(per) == {str(n) for n in sizes} and len(sizes) == 2
+    assert abs(out["projected_batch_s"] - sum(per[str(n)] * c for n, c in sizes.items())) <= 1e-12
+    assert abs(out["assemblies_per_s"] - len(prob.subdomains) / out["projected_batch_s"]) <= 1e-9
