@@ -79,7 +79,7 @@ def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
     _run_parallel(cmds)
     nvcc = os.path.join(cuda, "bin", "nvcc")
     links = [
-        [nvcc, *ARCH, "-shared", *objs_main, "-o", os.path.join(OUT, "libsc.so"), "-lcudart"],
+        [nvcc, *ARCH, "-shared", *objs_main, "-o", os.path.join(OUT, "libsc.so"), "-lcudart", "-lpthread"],
         [nvcc, *ARCH, "-shared", o_dense, "-o", os.path.join(OUT, "libsc_dense.so"),
          "-lcudart", "-lcublas"],
     ]

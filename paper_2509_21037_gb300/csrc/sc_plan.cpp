@@ -22,11 +22,14 @@
 //      walking the supernodes active on both chunks;
 //   7. flop and byte counters.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sc_internal.h"
@@ -197,9 +200,31 @@ std::string sc::analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
 
 sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<SubPlan> P(nsub);
+  // steps 1-5 of every subdomain on the host threads (each writes only its
+  // own SubPlan); errors are reported for the lowest failing index
+  std::vector<std::string> err(nsub);
+  {
+    std::atomic<int32_t> next{0};
+    std::atomic<bool> oom{false};
+    auto work = [&]() {
+      for (int32_t i; (i = next.fetch_add(1)) < nsub;) {
+        try {
+          err[i] = analyze(i, d[i], P[i]);
+        } catch (const std::bad_alloc &) {
+          oom = true;
+          return;
+        }
+      }
+    };
+    const int32_t T = std::max(1, std::min<int32_t>((int32_t)std::thread::hardware_concurrency(), nsub));
+    std::vector<std::thread> pool;
+    for (int32_t t = 1; t < T; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    if (oom) throw std::bad_alloc();
+  }
   for (int32_t i = 0; i < nsub; ++i) {
-    std::string e = analyze(i, d[i], P[i]);
-    if (!e.empty()) return fail(ctx, SC_ERR_INVALID_ARG, e);
+    if (!err[i].empty()) return fail(ctx, SC_ERR_INVALID_ARG, err[i]);
     if (d[i].m > 0 && !d[i].lambda_map) ctx->has_lambda = false;
     for (int32_t j = 0; j < d[i].m && d[i].lambda_map; ++j)
       if (d[i].lambda_map[j] < 0 || d[i].lambda_map[j] >= ctx->n_dual)
