@@ -74,7 +74,9 @@ void scf_free(scf_factor *f);
  * subdomain.  Arrays as in sc_subdomain_desc plus L's values; all host memory,
  * read only; q (n_dual doubles) is overwritten.  nthreads <= 0 uses every
  * hardware thread; threads split the subdomains and sum private dual vectors
- * in a fixed order.  Returns SCF_ERR_INVALID_ARG on bad sizes or maps. */
+ * in a fixed order.  Returns SCF_ERR_INVALID_ARG on bad sizes or maps, or
+ * on a pattern that is not CSC lower with the diagonal first and rows
+ * strictly ascending (checked on every call; scf_implicit_plan checks once). */
 typedef struct {
   int32_t n, m;
   const int64_t *L_colptr;

@@ -7,6 +7,7 @@
 // thread accumulating into its own dual vector (summed at the end), so the
 // result does not depend on thread timing.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -157,27 +158,62 @@ void run_one(const scf_apply_subdomain &s, const SubPlan &P, const double *lambd
   }
 }
 
-int check_subs(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual) {
-  if (nsub < 0 || n_dual < 0 || (nsub > 0 && !subs)) return SCF_ERR_INVALID_ARG;
-  for (int32_t i = 0; i < nsub; ++i) {
-    const scf_apply_subdomain &s = subs[i];
-    if (s.n < 0 || s.m < 0 || (s.n > 0 && (!s.L_colptr || !s.L_rowind || !s.L_val))) return SCF_ERR_INVALID_ARG;
-    if (s.m > 0 && (!s.Bt_colptr || !s.Bt_rowind || !s.Bt_sign || !s.lambda_map)) return SCF_ERR_INVALID_ARG;
-    for (int32_t j = 0; j < s.m; ++j)
-      if (s.lambda_map[j] < 0 || s.lambda_map[j] >= n_dual) return SCF_ERR_INVALID_ARG;
-    for (int32_t j = 0; j < s.m; ++j)
-      for (int32_t e = s.Bt_colptr[j]; e < s.Bt_colptr[j + 1]; ++e)
-        if (s.Bt_rowind[e] < 0 || s.Bt_rowind[e] >= s.n) return SCF_ERR_INVALID_ARG;
+// Every index the solves form stays in range: L is CSC lower with the
+// diagonal first and rows strictly ascending below it, B^T's column pointers
+// start at 0 and do not decrease, its rows and the multiplier map are in
+// range.
+bool check_one(const scf_apply_subdomain &s, int64_t n_dual) {
+  if (s.n < 0 || s.m < 0 || (s.n > 0 && (!s.L_colptr || !s.L_rowind || !s.L_val))) return false;
+  if (s.m > 0 && (!s.Bt_colptr || !s.Bt_rowind || !s.Bt_sign || !s.lambda_map)) return false;
+  if (s.n > 0) {
+    if (s.L_colptr[0] != 0) return false;
+    for (int32_t c = 0; c < s.n; ++c) {
+      const int64_t a = s.L_colptr[c], b = s.L_colptr[c + 1];
+      if (b <= a || s.L_rowind[a] != c) return false;
+      for (int64_t e = a + 1; e < b; ++e)
+        if (s.L_rowind[e] <= s.L_rowind[e - 1] || s.L_rowind[e] >= s.n) return false;
+    }
   }
-  return SCF_OK;
+  if (s.m > 0) {
+    if (s.Bt_colptr[0] != 0) return false;
+    for (int32_t j = 0; j < s.m; ++j)
+      if (s.Bt_colptr[j + 1] < s.Bt_colptr[j]) return false;
+  }
+  for (int32_t j = 0; j < s.m; ++j)
+    if (s.lambda_map[j] < 0 || s.lambda_map[j] >= n_dual) return false;
+  for (int32_t j = 0; j < s.m; ++j)
+    for (int32_t e = s.Bt_colptr[j]; e < s.Bt_colptr[j + 1]; ++e)
+      if (s.Bt_rowind[e] < 0 || s.Bt_rowind[e] >= s.n) return false;
+  return true;
+}
+
+int32_t thread_count(int32_t nthreads, int32_t nsub) {
+  const int32_t T = nthreads > 0 ? nthreads : (int32_t)std::max(1u, std::thread::hardware_concurrency());
+  return std::max(1, std::min(T, std::max(nsub, 1)));
+}
+
+// check_one for every subdomain, on the host threads.
+int check_subs(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, int32_t nthreads) {
+  if (nsub < 0 || n_dual < 0 || (nsub > 0 && !subs)) return SCF_ERR_INVALID_ARG;
+  std::atomic<bool> ok{true};
+  std::atomic<int32_t> next{0};
+  auto work = [&]() {
+    for (int32_t i; ok && (i = next.fetch_add(1)) < nsub;)
+      if (!check_one(subs[i], n_dual)) ok = false;
+  };
+  const int32_t T = thread_count(nthreads, nsub);
+  std::vector<std::thread> pool;
+  for (int32_t t = 1; t < T; ++t) pool.emplace_back(work);
+  work();
+  for (auto &th : pool) th.join();
+  return ok ? SCF_OK : SCF_ERR_INVALID_ARG;
 }
 
 // Threads over subdomains, each summing into its own dual vector; the vectors
 // are added in thread order, so the result does not depend on timing.
 template <class F>
 void over_threads(int32_t nsub, int64_t n_dual, double *q, int32_t nthreads, F &&body) {
-  int32_t T = nthreads > 0 ? nthreads : (int32_t)std::max(1u, std::thread::hardware_concurrency());
-  T = std::max(1, std::min(T, std::max(nsub, 1)));
+  const int32_t T = thread_count(nthreads, nsub);
   std::vector<std::vector<double>> qs(T, std::vector<double>(n_dual, 0.0));
   std::vector<std::thread> pool;
   for (int32_t t = 0; t < T; ++t) pool.emplace_back([&, t]() { body(t, T, qs[t].data()); });
@@ -199,9 +235,9 @@ extern "C" {
 
 int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, const double *lambda,
                        double *q, int32_t nthreads) {
-  const int rc = check_subs(nsub, subs, n_dual);
-  if (rc != SCF_OK) return rc;
   if (n_dual > 0 && (!lambda || !q)) return SCF_ERR_INVALID_ARG;
+  const int rc = check_subs(nsub, subs, n_dual, nthreads);
+  if (rc != SCF_OK) return rc;
   over_threads(nsub, n_dual, q, nthreads, [&](int32_t t, int32_t T, double *qt) {
     std::vector<double> x;
     for (int32_t i = t; i < nsub; i += T) apply_one(subs[i], lambda, qt, x);
@@ -212,7 +248,7 @@ int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_
 int scf_implicit_plan(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, scf_implicit **out) {
   if (!out) return SCF_ERR_INVALID_ARG;
   *out = nullptr;
-  const int rc = check_subs(nsub, subs, n_dual);
+  const int rc = check_subs(nsub, subs, n_dual, 0);
   if (rc != SCF_OK) return rc;
   scf_implicit *p = new (std::nothrow) scf_implicit();
   if (!p) return SCF_ERR_OOM;

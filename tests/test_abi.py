@@ -539,3 +539,38 @@ def test_plan_predicts_the_structure_of_Y(name, prob):
         kept_total += kept.sum()
         nnz_total += nz.sum()
     assert nnz_total > 0 and kept_total >= nnz_total
+
+
+@pytest.mark.parametrize("case", ["L_row_out_of_range", "L_diag_not_first", "L_rows_unsorted", "L_colptr_start",
+                                  "Bt_colptr_decreasing", "Bt_row_out_of_range", "lambda_out_of_range"])
+def test_host_implicit_apply_rejects_bad_patterns(case):
+    """Both host implicit entry points check every index the solves form
+    (scf_implicit_apply on each call, scf_implicit_plan once)."""
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    f = fs[2]
+    L = host.HostFactor(f.L.n, f.L.colptr.copy(), f.L.rowind.copy(), f.L.values, f.L.perm)
+    btc, btr, lam = f.bt_colptr.copy(), f.bt_rowind.copy(), f.lambda_map.copy()
+    c = 7
+    a = int(L.colptr[c])
+    if case == "L_row_out_of_range":
+        L.rowind[int(L.colptr[c + 1]) - 1] = f.n
+    elif case == "L_diag_not_first":
+        L.rowind[a], L.rowind[a + 1] = L.rowind[a + 1], L.rowind[a]
+    elif case == "L_rows_unsorted":
+        L.rowind[a + 1], L.rowind[a + 2] = L.rowind[a + 2], L.rowind[a + 1]
+    elif case == "L_colptr_start":
+        L.colptr[0] = 1
+    elif case == "Bt_colptr_decreasing":
+        btc[3] = btc[5]
+    elif case == "Bt_row_out_of_range":
+        btr[4] = f.n
+    else:
+        lam[0] = prob.n_dual
+    bad = host.FactoredSubdomain(L=L, bt_colptr=btc, bt_rowind=btr, bt_sign=f.bt_sign, lambda_map=lam)
+    subs = fs[:2] + [bad] + fs[3:]
+    x = np.ones(prob.n_dual)
+    with pytest.raises(RuntimeError):
+        host.ImplicitApply(subs, prob.n_dual, planned=False)(x)
+    with pytest.raises(RuntimeError):
+        host.ImplicitApply(subs, prob.n_dual, planned=True)
