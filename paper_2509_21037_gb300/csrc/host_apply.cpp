@@ -201,26 +201,45 @@ int check_subs(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, in
     for (int32_t i; ok && (i = next.fetch_add(1)) < nsub;)
       if (!check_one(subs[i], n_dual)) ok = false;
   };
-  const int32_t T = thread_count(nthreads, nsub);
-  std::vector<std::thread> pool;
-  for (int32_t t = 1; t < T; ++t) pool.emplace_back(work);
-  work();
-  for (auto &th : pool) th.join();
+  try {
+    const int32_t T = thread_count(nthreads, nsub);
+    std::vector<std::thread> pool;
+    for (int32_t t = 1; t < T; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+  } catch (const std::bad_alloc &) {
+    return SCF_ERR_OOM;
+  }
   return ok ? SCF_OK : SCF_ERR_INVALID_ARG;
 }
 
 // Threads over subdomains, each summing into its own dual vector; the vectors
 // are added in thread order, so the result does not depend on timing.
+// Returns SCF_ERR_OOM (q untouched) if a host allocation fails.
 template <class F>
-void over_threads(int32_t nsub, int64_t n_dual, double *q, int32_t nthreads, F &&body) {
-  const int32_t T = thread_count(nthreads, nsub);
-  std::vector<std::vector<double>> qs(T, std::vector<double>(n_dual, 0.0));
-  std::vector<std::thread> pool;
-  for (int32_t t = 0; t < T; ++t) pool.emplace_back([&, t]() { body(t, T, qs[t].data()); });
-  for (auto &th : pool) th.join();
-  std::memset(q, 0, sizeof(double) * (size_t)n_dual);
-  for (int32_t t = 0; t < T; ++t)
-    for (int64_t k = 0; k < n_dual; ++k) q[k] += qs[t][k];
+int over_threads(int32_t nsub, int64_t n_dual, double *q, int32_t nthreads, F &&body) {
+  try {
+    const int32_t T = thread_count(nthreads, nsub);
+    std::vector<std::vector<double>> qs(T, std::vector<double>(n_dual, 0.0));
+    std::atomic<bool> oom{false};
+    std::vector<std::thread> pool;
+    for (int32_t t = 0; t < T; ++t)
+      pool.emplace_back([&, t]() {
+        try {
+          body(t, T, qs[t].data());
+        } catch (const std::bad_alloc &) {
+          oom = true;
+        }
+      });
+    for (auto &th : pool) th.join();
+    if (oom) return SCF_ERR_OOM;
+    std::memset(q, 0, sizeof(double) * (size_t)n_dual);
+    for (int32_t t = 0; t < T; ++t)
+      for (int64_t k = 0; k < n_dual; ++k) q[k] += qs[t][k];
+  } catch (const std::bad_alloc &) {
+    return SCF_ERR_OOM;
+  }
+  return SCF_OK;
 }
 
 }  // namespace
@@ -238,11 +257,10 @@ int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_
   if (n_dual > 0 && (!lambda || !q)) return SCF_ERR_INVALID_ARG;
   const int rc = check_subs(nsub, subs, n_dual, nthreads);
   if (rc != SCF_OK) return rc;
-  over_threads(nsub, n_dual, q, nthreads, [&](int32_t t, int32_t T, double *qt) {
+  return over_threads(nsub, n_dual, q, nthreads, [&](int32_t t, int32_t T, double *qt) {
     std::vector<double> x;
     for (int32_t i = t; i < nsub; i += T) apply_one(subs[i], lambda, qt, x);
   });
-  return SCF_OK;
 }
 
 int scf_implicit_plan(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, scf_implicit **out) {
@@ -268,11 +286,10 @@ int scf_implicit_plan(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_d
 int scf_implicit_run(const scf_implicit *p, const double *lambda, double *q, int32_t nthreads) {
   if (!p || (p->n_dual > 0 && (!lambda || !q))) return SCF_ERR_INVALID_ARG;
   const int32_t nsub = (int32_t)p->subs.size();
-  over_threads(nsub, p->n_dual, q, nthreads, [&](int32_t t, int32_t T, double *qt) {
+  return over_threads(nsub, p->n_dual, q, nthreads, [&](int32_t t, int32_t T, double *qt) {
     std::vector<double> x, buf;
     for (int32_t i = t; i < nsub; i += T) run_one(p->subs[i], p->plans[i], lambda, qt, x, buf);
   });
-  return SCF_OK;
 }
 
 void scf_implicit_free(scf_implicit *p) { delete p; }

@@ -285,37 +285,21 @@ bool numeric_supernodal(const scf_factor &F, const std::vector<double> &av, doub
   return true;
 }
 
-}  // namespace
-
-extern "C" {
-
-int scf_analyze(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, int32_t nfixed, const int32_t *fixed,
-                const int32_t *perm_in, int32_t do_postorder, scf_factor **out) {
-  if (!out) return SCF_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (n < 0 || nfixed < 0 || (nfixed > 0 && !fixed) || (n > 0 && (!K_colptr || !K_rowind)))
-    return SCF_ERR_INVALID_ARG;
-  if (n > 0) {
-    if (K_colptr[0] != 0) return SCF_ERR_INVALID_ARG;
-    for (int32_t c = 0; c < n; ++c)
-      if (K_colptr[c + 1] < K_colptr[c]) return SCF_ERR_INVALID_ARG;
-    for (int64_t e = 0; e < K_colptr[n]; ++e)
-      if (K_rowind[e] < 0 || K_rowind[e] >= n) return SCF_ERR_INVALID_ARG;
-  }
-  scf_factor *F = new (std::nothrow) scf_factor();
-  if (!F) return SCF_ERR_OOM;
+// Symbolic stage into F (steps 1-5 of the header); F's vectors are filled here.
+int analyze_into(scf_factor *F, int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, int32_t nfixed,
+                 const int32_t *fixed, const int32_t *perm_in, int32_t do_postorder) {
   F->n = n;
   F->nnzK = n > 0 ? K_colptr[n] : 0;
   std::vector<char> is_fixed(n, 0);
   for (int32_t k = 0; k < nfixed; ++k) {
-    if (fixed[k] < 0 || fixed[k] >= n) { delete F; return SCF_ERR_INVALID_ARG; }
+    if (fixed[k] < 0 || fixed[k] >= n) return SCF_ERR_INVALID_ARG;
     is_fixed[fixed[k]] = 1;
   }
   std::vector<int32_t> perm(n);
   if (perm_in) {
     std::vector<char> seen(n, 0);
     for (int32_t i = 0; i < n; ++i) {
-      if (perm_in[i] < 0 || perm_in[i] >= n || seen[perm_in[i]]) { delete F; return SCF_ERR_INVALID_ARG; }
+      if (perm_in[i] < 0 || perm_in[i] >= n || seen[perm_in[i]]) return SCF_ERR_INVALID_ARG;
       seen[perm_in[i]] = 1; perm[i] = perm_in[i];
     }
   } else {
@@ -379,6 +363,38 @@ int scf_analyze(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, int
   F->colptr.swap(cp);
   F->rowind.swap(ri);
   F->val.assign(F->rowind.size(), 0.0);
+  return SCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scf_analyze(int32_t n, const int64_t *K_colptr, const int32_t *K_rowind, int32_t nfixed, const int32_t *fixed,
+                const int32_t *perm_in, int32_t do_postorder, scf_factor **out) {
+  if (!out) return SCF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || nfixed < 0 || (nfixed > 0 && !fixed) || (n > 0 && (!K_colptr || !K_rowind)))
+    return SCF_ERR_INVALID_ARG;
+  if (n > 0) {
+    if (K_colptr[0] != 0) return SCF_ERR_INVALID_ARG;
+    for (int32_t c = 0; c < n; ++c)
+      if (K_colptr[c + 1] < K_colptr[c]) return SCF_ERR_INVALID_ARG;
+    for (int64_t e = 0; e < K_colptr[n]; ++e)
+      if (K_rowind[e] < 0 || K_rowind[e] >= n) return SCF_ERR_INVALID_ARG;
+  }
+  scf_factor *F = new (std::nothrow) scf_factor();
+  if (!F) return SCF_ERR_OOM;
+  try {
+    const int rc = analyze_into(F, n, K_colptr, K_rowind, nfixed, fixed, perm_in, do_postorder);
+    if (rc != SCF_OK) {
+      delete F;
+      return rc;
+    }
+  } catch (const std::bad_alloc &) {
+    delete F;
+    return SCF_ERR_OOM;
+  }
   *out = F;
   return SCF_OK;
 }

@@ -33,6 +33,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <new>
+
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -633,13 +635,20 @@ sc_status sci_plan(sci_ctx **out, int32_t nsub, const sc_subdomain_desc *subdoma
                    const sci_options *opt) {
   if (!out) return SC_ERR_INVALID_ARG;
   *out = nullptr;
-  sci_ctx *ctx = new sci_ctx();
+  sci_ctx *ctx = new (std::nothrow) sci_ctx();
+  if (!ctx) return SC_ERR_OOM;
   *out = ctx;
   if (nsub < 0 || (nsub > 0 && !subdomains) || n_dual < 0)
     return ifail(ctx, SC_ERR_INVALID_ARG, "nsub < 0, n_dual < 0 or subdomains NULL");
   ctx->nsub = nsub;
   ctx->n_dual = n_dual;
-  return build(ctx, nsub, subdomains, opt ? opt->cluster_min_work : -1);
+  try {
+    return build(ctx, nsub, subdomains, opt ? opt->cluster_min_work : -1);
+  } catch (const std::bad_alloc &) {
+    return ifail(ctx, SC_ERR_OOM, "host allocation failed while planning");
+  } catch (...) {
+    return ifail(ctx, SC_ERR_INTERNAL, "unexpected exception while planning");
+  }
 }
 
 sc_status sci_get_sizes(const sci_ctx *ctx, sci_sizes *s) {

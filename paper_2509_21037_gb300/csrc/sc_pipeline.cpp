@@ -11,6 +11,8 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -93,6 +95,10 @@ sc_status factor_chunk(scp_ctx *ctx, int32_t c, double *dst) {
   return SC_OK;
 }
 
+sc_status create_impl(scp_ctx *ctx, int32_t nsub, const scp_subdomain *subs, int32_t nchunks,
+                      const scp_chunk *chunks, int32_t nthreads);
+sc_status run_impl(scp_ctx *ctx, void *stream, scp_times *times);
+
 }  // namespace
 
 extern "C" {
@@ -100,8 +106,31 @@ extern "C" {
 sc_status scp_create(scp_ctx **out, int32_t nsub, const scp_subdomain *subs, int32_t nchunks,
                      const scp_chunk *chunks, int32_t nthreads) {
   if (!out) return SC_ERR_INVALID_ARG;
-  scp_ctx *ctx = new scp_ctx();
+  scp_ctx *ctx = new (std::nothrow) scp_ctx();
   *out = ctx;
+  if (!ctx) return SC_ERR_INTERNAL;
+  try {
+    return create_impl(ctx, nsub, subs, nchunks, chunks, nthreads);
+  } catch (const std::exception &e) {
+    return pfail(ctx, SC_ERR_INTERNAL, std::string("scp_create: ") + e.what());
+  }
+}
+
+sc_status scp_run(scp_ctx *ctx, void *stream, scp_times *times) {
+  if (!ctx) return SC_ERR_INVALID_ARG;
+  try {
+    return run_impl(ctx, stream, times);
+  } catch (const std::exception &e) {
+    return pfail(ctx, SC_ERR_INTERNAL, std::string("scp_run: ") + e.what());
+  }
+}
+
+}  // extern "C"
+
+namespace {
+
+sc_status create_impl(scp_ctx *ctx, int32_t nsub, const scp_subdomain *subs, int32_t nchunks,
+                      const scp_chunk *chunks, int32_t nthreads) {
   if (nsub < 0 || nchunks < 0 || (nsub > 0 && !subs) || (nchunks > 0 && !chunks))
     return pfail(ctx, SC_ERR_INVALID_ARG, "negative counts or NULL arrays");
   ctx->subs.assign(subs, subs + nsub);
@@ -180,8 +209,7 @@ sc_status scp_create(scp_ctx **out, int32_t nsub, const scp_subdomain *subs, int
   return SC_OK;
 }
 
-sc_status scp_run(scp_ctx *ctx, void *stream, scp_times *times) {
-  if (!ctx) return SC_ERR_INVALID_ARG;
+sc_status run_impl(scp_ctx *ctx, void *stream, scp_times *times) {
   if (!ctx->copy) return pfail(ctx, SC_ERR_STATE, "scp_create did not complete");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int32_t nc = (int32_t)ctx->chunks.size();
@@ -242,6 +270,10 @@ sc_status scp_run(scp_ctx *ctx, void *stream, scp_times *times) {
   }
   return SC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 const char *scp_last_error(const scp_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
