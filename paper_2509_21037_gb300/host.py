@@ -278,8 +278,14 @@ def factorize_problem(subdomains, threads: int = 0, leaf: int = 8) -> List[Facto
     if threads == 1 or len(uniq) == 1:
         facs = [work(sd) for sd in uniq]
     else:
+        # largest first (the factorisation cost grows like n^2 in 3D, n^1.5 in 2D), so that
+        # the biggest subdomains do not start last and set the time of the whole batch
+        cost = [sd.K.shape[0] ** (2.0 if sd.grid[2] > 1 else 1.5) for sd in uniq]
+        order = sorted(range(len(uniq)), key=lambda j: -cost[j])
+        facs = [None] * len(uniq)
         with ThreadPoolExecutor(max_workers=threads or None) as ex:
-            facs = list(ex.map(work, uniq))
+            for j, fac in zip(order, ex.map(work, [uniq[j] for j in order])):
+                facs[j] = fac
     out = []
     for sd in subdomains:
         k = sd.key if sd.key is not None else id(sd)
