@@ -155,11 +155,14 @@ void postorder(int32_t n, const std::vector<int32_t> &parent, std::vector<int32_
 // its rounding error) and added with an error-free two-sum; the errors go to
 // wl.  Four columns per pass, so that w and wl are loaded and stored once for
 // four products; the accumulation order is that of four single passes.
+// Init: w and wl start from zero instead of being read (the same numbers:
+// 0 + p is p exactly and its two-sum error is 0).
+template <bool Init>
 void dd_axpy4(double *__restrict w, double *__restrict wl, const double *__restrict v0,
               const double *__restrict v1, const double *__restrict v2, const double *__restrict v3,
               double b0, double b1, double b2, double b3, int64_t len) {
   for (int64_t a = 0; a < len; ++a) {
-    double h = w[a], l = wl[a];
+    double h = Init ? 0.0 : w[a], l = Init ? 0.0 : wl[a];
     const double x[4] = {v0[a], v1[a], v2[a], v3[a]};
     const double b[4] = {b0, b1, b2, b3};
     for (int u = 0; u < 4; ++u) {
@@ -175,25 +178,34 @@ void dd_axpy4(double *__restrict w, double *__restrict wl, const double *__restr
   }
 }
 
+template <bool Init>
 void dd_axpy1(double *__restrict w, double *__restrict wl, const double *__restrict v, double b, int64_t len) {
   for (int64_t a = 0; a < len; ++a) {
-    const double h = w[a];
+    const double h = Init ? 0.0 : w[a];
     const double p = v[a] * b;
     const double pe = std::fma(v[a], b, -p);
     const double s = h + p;
     const double bb = s - h;
-    wl[a] += ((h - (s - bb)) + (p - bb)) + pe;
+    wl[a] = (Init ? 0.0 : wl[a]) + (((h - (s - bb)) + (p - bb)) + pe);
     w[a] = s;
   }
 }
 
-// w + wl += sign * sum_{s < ns} V[s] * V[s][off], V[s] = cols[s] (rows off..off+len)
-void dd_update(double *w, double *wl, const double *const *cols, int32_t ns, int64_t off, int64_t len, double sign) {
+// w + wl += sign * sum_{s < ns} V[s] * V[s][off], V[s] = cols[s] (rows off..off+len);
+// with init (ns >= 1) w + wl is the sum alone, its previous contents unread.
+void dd_update(double *w, double *wl, const double *const *cols, int32_t ns, int64_t off, int64_t len, double sign,
+               bool init = false) {
   int32_t s = 0;
-  for (; s + 4 <= ns; s += 4)
-    dd_axpy4(w, wl, cols[s] + off, cols[s + 1] + off, cols[s + 2] + off, cols[s + 3] + off, sign * cols[s][off],
-             sign * cols[s + 1][off], sign * cols[s + 2][off], sign * cols[s + 3][off], len);
-  for (; s < ns; ++s) dd_axpy1(w, wl, cols[s] + off, sign * cols[s][off], len);
+  for (; s + 4 <= ns; s += 4) {
+    const double *const v[4] = {cols[s] + off, cols[s + 1] + off, cols[s + 2] + off, cols[s + 3] + off};
+    const double b[4] = {sign * cols[s][off], sign * cols[s + 1][off], sign * cols[s + 2][off], sign * cols[s + 3][off]};
+    if (init && s == 0) dd_axpy4<true>(w, wl, v[0], v[1], v[2], v[3], b[0], b[1], b[2], b[3], len);
+    else dd_axpy4<false>(w, wl, v[0], v[1], v[2], v[3], b[0], b[1], b[2], b[3], len);
+  }
+  for (; s < ns; ++s) {
+    if (init && s == 0) dd_axpy1<true>(w, wl, cols[s] + off, sign * cols[s][off], len);
+    else dd_axpy1<false>(w, wl, cols[s] + off, sign * cols[s][off], len);
+  }
 }
 
 // Numeric stage, supernodal left-looking, into L (nnz values, CSC layout of
@@ -241,9 +253,7 @@ bool numeric_supernodal(const scf_factor &F, const std::vector<double> &av, doub
       for (int32_t s = 0; s < nsk; ++s) cols[s] = L + cp[fk + s] + (p - s);   // rows RK[p..nrk)
       const int64_t len = nrk - p;
       for (int64_t b = 0; b < p2 - p; ++b) {
-        std::fill(wh.begin() + b, wh.begin() + len, 0.0);
-        std::fill(wl.begin() + b, wl.begin() + len, 0.0);
-        dd_update(wh.data() + b, wl.data() + b, cols.data(), nsk, b, len - b, 1.0);
+        dd_update(wh.data() + b, wl.data() + b, cols.data(), nsk, b, len - b, 1.0, true);   // nsk >= 1
         double *ph = Ph.data() + (int64_t)(RK[p + b] - f) * nr, *pl = Pl.data() + (int64_t)(RK[p + b] - f) * nr;
         for (int64_t a = b; a < len; ++a) {
           const int32_t i = pos[RK[p + a]];
