@@ -466,13 +466,24 @@ def run_sc(args):
     t_gimpl, gimpl = _gpu_implicit(fs, prob.n_dual, Lv, lam, q, stream)
     impl = host.ImplicitApply(fs, prob.n_dual)
     lam_h = lam.cpu().numpy()
-    impl(lam_h)
+    q_host = impl(lam_h)
+    q_dev = q.cpu().numpy()
+    host_rel_diff = float(np.linalg.norm(q_host - q_dev) / np.linalg.norm(q_dev))
     t_impl = []
     for _ in range(5):
         t0 = time.perf_counter()
         impl(lam_h)
         t_impl.append(1e3 * (time.perf_counter() - t0))
     t_impl = statistics.median(t_impl)
+    # the column-by-column host form, for reference (the planned form above is the comparator)
+    impl_col = host.ImplicitApply(fs, prob.n_dual, planned=False)
+    impl_col(lam_h)
+    t_col = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        impl_col(lam_h)
+        t_col.append(1e3 * (time.perf_counter() - t0))
+    t_col = statistics.median(t_col)
     t_asm = sum(prep_ms) / len(prep_ms) + sum(trsm_ms) / len(trsm_ms) + sum(syrk_ms) / len(syrk_ms)
 
     # dominant kernel roofline (FP64 pipe)
@@ -506,6 +517,9 @@ def run_sc(args):
                          if t_impl > t_expl else None,
                          "t_assembly_ms": t_asm, "t_apply_explicit_gpu_ms": t_expl,
                          "t_apply_implicit_host_ms": t_impl, "implicit_host_threads": os.cpu_count(),
+                         "implicit_host_form": "planned: per supernode, symbolic work once",
+                         "implicit_host_rel_diff_vs_explicit": host_rel_diff,
+                         "t_apply_implicit_host_column_ms": t_col,
                          "iterations_vs_gpu_implicit": t_asm / (t_gimpl - t_expl) if t_gimpl > t_expl else None,
                          "t_apply_implicit_gpu_ms": t_gimpl,
                          "iterations_vs_gpu_implicit_fixed_apply": t_asm / (t_gimpl - t_fixed) if t_gimpl > t_fixed else None},
