@@ -203,12 +203,7 @@ class FETISolver:
         self.subs = subs
         self.nd = int(problem.n_dual)
         self.fs = list(factored) if factored is not None else host.factorize_problem(subs)
-        self.plan = sc.Plan(self.fs, self.nd, **(plan_kwargs or {})).upload(self.dev)
-        self.Lv = torch.from_numpy(sc.concat_L_values(self.fs)).to(self.dev)
-        self.F = self.plan.new_F(self.dev)
-        self.plan.assemble(self.Lv, self.F)
-        if self.plan.device_status() != 0:
-            raise RuntimeError("assembly reported a non-SPD factor")
+        self.plan, self.F = self._make_operator(plan_kwargs or {})
         self.R = [kernel_basis(sd) for sd in subs]
         self.kplus = [_KPlus(sd, f) for sd, f in zip(subs, self.fs)]
         # G = [B_i R_i] and the two sparse dual operators: the fixed-dof
@@ -253,10 +248,44 @@ class FETISolver:
         if precond != "none" and scaling == "bbt":
             self.W = self._sparse(*_coo(bbt_inverse(subs, self.nd)))
 
+    def _make_operator(self, plan_kwargs: dict):
+        """The library's plan and assembled F (tile-packed, on the device)."""
+        plan = sc.Plan(self.fs, self.nd, **plan_kwargs).upload(self.dev)
+        self.Lv = self.torch.from_numpy(sc.concat_L_values(self.fs)).to(self.dev)
+        F = plan.new_F(self.dev)
+        plan.assemble(self.Lv, F)
+        if plan.device_status() != 0:
+            raise RuntimeError("assembly reported a non-SPD factor")
+        return plan, F
+
+    def _events(self):
+        """A pair of timing events on the device's current stream (CUDA
+        events; a host clock with the same interface off CUDA)."""
+        if self.dev.type == "cuda":
+            return self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+        return _HostEvent(), _HostEvent()
+
+    def _rhs(self, loads):
+        """d = sum_i B_i K_i^+ f_i and e = [R_i^T f_i], kept for the last loads
+        object (a second solve of the same loads skips the host solves)."""
+        cached = getattr(self, "_rhs_cache", None)
+        if cached is not None and cached[0] is loads:
+            return cached[1], cached[2]
+        d = np.zeros(self.nd)
+        e = []
+        for sd, kp, R, f in zip(self.subs, self.kplus, self.R, loads):
+            np.add.at(d, np.asarray(sd.lambda_map, np.int64), sp.csc_matrix(sd.Bt).T @ kp(f))
+            e.append(R.T @ f)
+        d_t = self.torch.from_numpy(d).to(self.dev)
+        e_t = self.torch.from_numpy(np.concatenate(e)).to(self.dev)
+        self._rhs_cache = (loads, d_t, e_t)
+        return d_t, e_t
+
     def _sparse(self, r, c, v):
         t = self.torch
         idx = t.from_numpy(np.vstack([r, c]).astype(np.int64))
-        return t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd)).coalesce().to(self.dev)
+        return t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd),
+                                   check_invariants=True).coalesce().to(self.dev)
 
     def apply_F(self, x):
         """q = F x (library sc_apply, then the fixed-dof correction)."""
@@ -282,18 +311,15 @@ class FETISolver:
             y = t.sparse.mm(self.W, y[:, None])[:, 0]
         return self.project(y)
 
-    def solve(self, loads: Sequence[np.ndarray], tol: float = 1e-10, maxit: int = 1000) -> FETIResult:
+    def solve(self, loads: Sequence[np.ndarray], tol: float = 1e-10, maxit: int = 1000,
+              recover: bool = True) -> FETIResult:
+        """PCPG to ||w_k|| / ||w_0|| < tol.  recover=False skips the primal
+        recovery and its checks (alpha, u, continuity and equilibrium are
+        then empty or NaN): a solve for the iteration count or the time."""
         t = self.torch
         subs, nd = self.subs, self.nd
-        # d = sum_i B_i K_i^+ f_i, e = [R_i^T f_i]
-        d = np.zeros(nd)
-        e = []
-        for sd, kp, R, f in zip(subs, self.kplus, self.R, loads):
-            np.add.at(d, np.asarray(sd.lambda_map, np.int64), sp.csc_matrix(sd.Bt).T @ kp(f))
-            e.append(R.T @ f)
-        d_t = t.from_numpy(d).to(self.dev)
-        e_t = t.from_numpy(np.concatenate(e)).to(self.dev)
-        ev0, ev1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+        d_t, e_t = self._rhs(loads)
+        ev0, ev1 = self._events()
         ev0.record()
         lam = self.G @ (self.GtG_pinv @ e_t)
         r = d_t - self.apply_F(lam)
@@ -317,9 +343,19 @@ class FETISolver:
         ev1.record()
         ev1.synchronize()
         solve_ms = ev0.elapsed_time(ev1)
+        lam_h = lam.cpu().numpy()
+        # one F application, timed alone
+        a0, a1 = self._events()
+        a0.record()
+        for _ in range(10):
+            self.apply_F(lam)
+        a1.record()
+        a1.synchronize()
+        apply_ms = a0.elapsed_time(a1) / 10
+        if not recover:
+            return FETIResult(lam_h, [], [], it, res, float("nan"), float("nan"), apply_ms, solve_ms)
         # alpha = (G^T G)^+ G^T (F lambda - d); u_i = K_i^+ (f_i - B_i^T lambda) + R_i alpha_i
         alpha = (self.GtG_pinv @ (self.G.T @ (self.apply_F(lam) - d_t))).cpu().numpy()
-        lam_h = lam.cpu().numpy()
         us, al, k = [], [], 0
         for sd, kp, R, f in zip(subs, self.kplus, self.R, loads):
             a = alpha[k:k + R.shape[1]]
@@ -334,14 +370,20 @@ class FETISolver:
             np.add.at(jump, lm, sp.csc_matrix(sd.Bt).T @ u)
             eq = max(eq, np.linalg.norm(sd.K @ u - f + sp.csc_matrix(sd.Bt) @ lam_h[lm]) / max(np.linalg.norm(f), 1e-300))
         cont = np.linalg.norm(jump) / max(max(np.linalg.norm(u) for u in us), 1e-300)
-        # one F application, timed alone
-        a0, a1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
-        a0.record()
-        for _ in range(10):
-            self.apply_F(lam)
-        a1.record()
-        a1.synchronize()
-        return FETIResult(lam_h, al, us, it, res, float(cont), float(eq), a0.elapsed_time(a1) / 10, solve_ms)
+        return FETIResult(lam_h, al, us, it, res, float(cont), float(eq), apply_ms, solve_ms)
+
+
+class _HostEvent:
+    """Host-clock stand-in for a CUDA timing event (solver on a CPU device)."""
+
+    def record(self):
+        self.t = time.perf_counter()
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other) -> float:
+        return 1e3 * (other.t - self.t)
 
 
 def _coo(M):

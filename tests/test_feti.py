@@ -7,7 +7,7 @@ import scipy.sparse as sp
 
 import oracle
 import synth
-from paper_2509_21037_gb300 import feti
+from paper_2509_21037_gb300 import feti, host
 
 
 def test_kernel_bases_span_ker_K():
@@ -187,3 +187,60 @@ def test_scaled_preconditioners_cut_iterations():
         assert np.linalg.norm(lam - lam0) <= 1e-7 * np.linalg.norm(lam0)
     assert nD < nL < n0 // 3, (nD, nL, n0)
     assert _pcpg(F, G, d, e, ML)[1] > n0 and _pcpg(F, G, d, e, MD)[1] > n0
+
+
+class _DenseFETI(feti.FETISolver):
+    """feti.FETISolver's host-side logic on the CPU: the library's plan is
+    replaced by dense products with the oracle's operator (F = sum_i B_i
+    K_reg^-1 B_i^T scattered by the lambda maps; pack assembles the blocks
+    the same way), everything else -- projector, fixed-dof correction,
+    scalings, preconditioners, PCPG, recovery -- is the solver's own code."""
+
+    def _make_operator(self, plan_kwargs):
+        import torch
+        nd = self.nd
+        Fd = np.zeros((nd, nd))
+        for sd, Fi in zip(self.subs, oracle.dual_operators(self.subs)):
+            lm = np.asarray(sd.lambda_map)
+            Fd[np.ix_(lm, lm)] += Fi
+        subs = self.subs
+
+        class _Plan:
+            def apply(self, F, x, q):
+                q.copy_(F @ x)
+
+            def pack(self, blocks, device):
+                M = np.zeros((nd, nd))
+                for sd, Bk in zip(subs, blocks):
+                    lm = np.asarray(sd.lambda_map)
+                    M[np.ix_(lm, lm)] += Bk
+                return torch.from_numpy(M)
+
+        return _Plan(), torch.from_numpy(Fd)
+
+
+def test_feti_solver_logic_on_the_cpu():
+    """The solver with each preconditioner reaches the multipliers of a plain
+    projected CG on the oracle's operator, recovers a continuous and
+    equilibrated primal solution, orders the iteration counts Dirichlet <
+    lumped < none, and a solve without recovery (the bench's warm-up) gives
+    the same iterations and multipliers."""
+    import math
+    pytest = __import__("pytest")
+    pytest.importorskip("torch")
+    prob = synth.cube_heat_3d(2, 4, coef_seed=3)
+    loads = feti.compatible_loads(prob, seed=5)
+    fs = host.factorize_problem(prob.subdomains)
+    F, G, d, e = _dual_problem(prob, loads)
+    lam_ref, _ = _pcpg(F, G, d, e, tol=1e-12)
+    its = {}
+    for pc in ("none", "lumped", "dirichlet"):
+        s = _DenseFETI(prob, fs, device="cpu", precond=pc)
+        r0 = s.solve(loads, tol=1e-10, recover=False)
+        assert math.isnan(r0.continuity) and r0.u == [] and r0.solve_ms >= 0 and r0.apply_ms >= 0
+        r = s.solve(loads, tol=1e-10)
+        assert r.iterations == r0.iterations and np.array_equal(r.lam, r0.lam)
+        assert np.linalg.norm(r.lam - lam_ref) <= 1e-7 * np.linalg.norm(lam_ref)
+        assert r.continuity <= 1e-8 and r.equilibrium <= 1e-8
+        its[pc] = r.iterations
+    assert its["dirichlet"] < its["lumped"] < its["none"], its
