@@ -52,6 +52,8 @@ def factor_lib() -> ctypes.CDLL:
         lib.scf_implicit_plan.restype = c_int
         lib.scf_implicit_run.argtypes = [c_vp, c_vp, c_vp, c_i32]
         lib.scf_implicit_run.restype = c_int
+        lib.scf_solve.argtypes = [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]
+        lib.scf_solve.restype = c_int
         lib.scf_implicit_free.argtypes = [c_vp]
         lib.scf_implicit_free.restype = None
         lib._typed = True

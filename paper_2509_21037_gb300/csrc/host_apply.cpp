@@ -294,4 +294,30 @@ int scf_implicit_run(const scf_implicit *p, const double *lambda, double *q, int
 
 void scf_implicit_free(scf_implicit *p) { delete p; }
 
+int scf_solve(int32_t n, const int64_t *L_colptr, const int32_t *L_rowind, const double *L_val, const double *b,
+              double *x) {
+  if (n < 0 || (n > 0 && (!L_colptr || !L_rowind || !L_val || !b || !x))) return SCF_ERR_INVALID_ARG;
+  scf_apply_subdomain s;
+  std::memset(&s, 0, sizeof s);
+  s.n = n;
+  s.L_colptr = L_colptr;
+  s.L_rowind = L_rowind;
+  s.L_val = L_val;
+  if (!check_one(s, 0)) return SCF_ERR_INVALID_ARG;
+  if (x != b) std::memcpy(x, b, sizeof(double) * (size_t)n);
+  for (int32_t c = 0; c < n; ++c) {                       // L y = b, column oriented
+    const int64_t a = L_colptr[c], e1 = L_colptr[c + 1];
+    const double yc = x[c] / L_val[a];
+    x[c] = yc;
+    for (int64_t e = a + 1; e < e1; ++e) x[L_rowind[e]] -= L_val[e] * yc;
+  }
+  for (int32_t c = n - 1; c >= 0; --c) {                   // L^T x = y, row oriented over L's columns
+    const int64_t a = L_colptr[c], e1 = L_colptr[c + 1];
+    double acc = x[c];
+    for (int64_t e = a + 1; e < e1; ++e) acc -= L_val[e] * x[L_rowind[e]];
+    x[c] = acc / L_val[a];
+  }
+  return SCF_OK;
+}
+
 }  // extern "C"

@@ -49,7 +49,6 @@ from typing import List, Optional, Sequence
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
-import scipy.sparse.linalg as spla
 
 from . import host, sc
 
@@ -148,19 +147,16 @@ def dirichlet_block(sd, S: Optional[np.ndarray] = None) -> np.ndarray:
 
 
 class _KPlus:
-    """x = K^+ b for one subdomain with its host factor: K_reg^{-1} b with
-    the fixed dofs zeroed."""
+    """x = K^+ b for one subdomain with its host factor: K_reg^{-1} b (two
+    host triangular solves, scf_solve) with the fixed dofs zeroed."""
 
     def __init__(self, sd, fs):
-        L = sp.csc_matrix((fs.L.values, fs.L.rowind, fs.L.colptr), shape=(fs.n, fs.n))
-        self.Lr = L.tocsr()
-        self.Ur = L.T.tocsr()
+        self.L = fs.L
         self.perm = fs.L.perm
         self.fixed = np.asarray(sd.fixed, np.int64)
 
     def __call__(self, b: np.ndarray) -> np.ndarray:
-        y = spla.spsolve_triangular(self.Lr, b[self.perm], lower=True)
-        w = spla.spsolve_triangular(self.Ur, y, lower=False)
+        w = host.solve_LLt(self.L, np.asarray(b, np.float64)[self.perm])
         x = np.empty_like(w)
         x[self.perm] = w
         x[self.fixed] = 0.0

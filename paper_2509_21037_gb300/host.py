@@ -115,6 +115,22 @@ def factorize(K: sp.spmatrix, fixed: Sequence[int], perm: Optional[np.ndarray] =
     return out
 
 
+def solve_LLt(L: HostFactor, b: np.ndarray) -> np.ndarray:
+    """x = L^-T L^-1 b in L's ordering (scf_solve: two sparse triangular
+    solves on the host)."""
+    b = np.ascontiguousarray(b, np.float64)
+    assert b.shape == (L.n,)
+    x = np.empty(L.n)
+    cp = np.ascontiguousarray(L.colptr, np.int64)
+    ri = np.ascontiguousarray(L.rowind, np.int32)
+    va = np.ascontiguousarray(L.values, np.float64)
+    rc = _native.factor_lib().scf_solve(L.n, cp.ctypes.data, ri.ctypes.data, va.ctypes.data, b.ctypes.data,
+                                        x.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"scf_solve failed with code {rc}")
+    return x
+
+
 class SymbolicFactor:
     """The symbolic stage alone (scf_analyze): the ordering and L's pattern
     for K's pattern, kept so that ``numeric`` runs only the numeric stage

@@ -192,3 +192,21 @@ def test_symbolic_and_numeric_reject_bad_input():
     bad.indices[5] = 40                                    # row index out of range
     with pytest.raises(RuntimeError):
         host.SymbolicFactor(bad, [0], perm=np.arange(12), postorder=False)
+
+
+def test_solve_LLt_against_scipy_triangular_solves():
+    """host.solve_LLt (scf_solve) against scipy's sparse triangular solves
+    on the same factor; bad patterns are refused."""
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(3)
+    for name, K, fixed, perm in CASES[:3]:
+        f = _factor(K, fixed, perm)
+        L = sp.csr_matrix(sp.csc_matrix((f.values, f.rowind, f.colptr), shape=(f.n, f.n)))
+        b = rng.standard_normal(f.n)
+        ref = spla.spsolve_triangular(L.T.tocsr(), spla.spsolve_triangular(L, b, lower=True), lower=False)
+        x = host.solve_LLt(f, b)
+        assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref), name
+    bad = host.HostFactor(f.n, f.colptr, f.rowind.copy(), f.values, f.perm)
+    bad.rowind[f.colptr[4]] += 1                           # column 4 no longer starts with its diagonal
+    with pytest.raises(RuntimeError):
+        host.solve_LLt(bad, b)
