@@ -207,16 +207,19 @@ sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_d
  * (sc_upload_plan), L_values_dev and F_dev, as for sc_assemble_batch.
  *   - Plans whose sizes.ws_bytes exceeds SC_STATIC_SCRATCH_BYTES are rejected
  *     with SC_ERR_OOM before anything is launched.
- *   - The array is allocated on every device that loads the library's module
- *     and stays allocated until the process exits.
- *   - The first call on a device looks up the array's device address (set-up,
- *     done once per device with that device current); make that first call
- *     before any stream capture.
- *   - Every call on a device shares the one array, which keeps the previous
- *     call's contents: calls that overlap on the GPU (other streams, other
- *     threads, other contexts) race and must be serialised by the caller.
- *   - The call synchronises `stream` and returns this call's device status
- *     (SC_OK or SC_ERR_NOT_SPD), so no sc_device_status call is needed.
+ *   - The array is allocated in every CUDA context that loads the library's
+ *     module (one copy per context, each at its own address) and stays
+ *     allocated until that context is destroyed; for a device's primary
+ *     context that is the end of the process.
+ *   - Every call looks up the array's address in the calling thread's current
+ *     context, so calls under different contexts use their own copies.
+ *   - Every call in one context shares that context's array, which keeps the
+ *     previous call's contents: calls that overlap on the GPU (other streams,
+ *     other threads) race and must be serialised by the caller.
+ *   - The call synchronises `stream` (it reads the device status word back
+ *     into host memory) and returns this call's device status (SC_OK or
+ *     SC_ERR_NOT_SPD), so no sc_device_status call is needed.
+ *   - F_dev must be 8-byte aligned, as for sc_assemble_batch.
  * No cudaMalloc, cudaFree or allocating library routine is called. */
 sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_values_dev, double *F_dev, void *stream);
 

@@ -91,6 +91,14 @@ typedef struct {
 int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, const double *lambda,
                        double *q, int32_t nthreads);
 
+/* x = L^-T L^-1 b for one factor in CSC (the arrays of scf_export, L's
+ * ordering): a forward and a backward sparse triangular solve on the host.
+ * b and x are n doubles, host memory; x may equal b.  SCF_ERR_INVALID_ARG on
+ * NULL arrays or a pattern that is not CSC lower with the diagonal first and
+ * rows strictly ascending. */
+int scf_solve(int32_t n, const int64_t *L_colptr, const int32_t *L_rowind, const double *L_val, const double *b,
+              double *x);
+
 /* The same product with its symbolic work done once (the implicit approach's
  * own preprocessing, paper Sec. 2.2).  scf_implicit_plan reads the patterns:
  * per subdomain the supernodes of L (runs of columns with one shared
@@ -105,14 +113,6 @@ int scf_implicit_apply(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_
  * threading and fixed summation order as scf_implicit_apply; the results of
  * the two agree to rounding.  SCF_ERR_INVALID_ARG on bad sizes, maps or row
  * indices; SCF_ERR_OOM if the plan cannot be allocated (*out stays NULL). */
-/* x = L^-T L^-1 b for one factor in CSC (the arrays of scf_export, L's
- * ordering): a forward and a backward sparse triangular solve on the host.
- * b and x are n doubles, host memory; x may equal b.  SCF_ERR_INVALID_ARG on
- * NULL arrays or a pattern that is not CSC lower with the diagonal first and
- * rows strictly ascending. */
-int scf_solve(int32_t n, const int64_t *L_colptr, const int32_t *L_rowind, const double *L_val, const double *b,
-              double *x);
-
 typedef struct scf_implicit scf_implicit;
 int scf_implicit_plan(int32_t nsub, const scf_apply_subdomain *subs, int64_t n_dual, scf_implicit **out);
 int scf_implicit_run(const scf_implicit *plan, const double *lambda, double *q, int32_t nthreads);

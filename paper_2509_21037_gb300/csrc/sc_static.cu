@@ -10,14 +10,16 @@
 // into the library.
 //
 // The array below is allocated by the CUDA runtime when this module is
-// loaded on a device and stays allocated on every device that loaded it until
-// the process exits.  In host code its name is only a host-side stand-in, so
-// its device address is fetched once per device with cudaGetSymbolAddress
-// (with that device current) and then passed to the kernels.
+// loaded into a CUDA context and stays allocated until that context is
+// destroyed (for the primary context of a device: until the process exits).
+// Every context that loads the module has its own copy at its own address.
+// In host code the array's name is only a host-side stand-in, so its device
+// address is looked up with cudaGetSymbolAddress in the calling thread's
+// current context on every call (a cheap host-side lookup) and then passed to
+// the kernels; an address cached from another context would not be valid.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "sc_internal.h"
@@ -30,10 +32,6 @@ constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // SC_STATIC_SCRATCH_
 static_assert(kStaticScratchBytes == SC_STATIC_SCRATCH_BYTES, "keep sc.h in step");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
 
 sc_status static_fail(sc_ctx *ctx, cudaError_t e, const char *where) {
   return fail(ctx, SC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -51,23 +49,13 @@ extern "C" sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_value
                     std::to_string(kStaticScratchBytes) +
                     "-byte static scratch; split the batch or use sc_assemble_batch with a caller workspace");
   if (ctx->sizes.L_values > 0 && !L_values_dev) return fail(ctx, SC_ERR_INVALID_ARG, "L_values_dev is NULL");
-  if (ctx->sizes.F_doubles > 0 && !F_dev) return fail(ctx, SC_ERR_INVALID_ARG, "F_dev is NULL");
+  if (ctx->sizes.F_doubles > 0 && (!F_dev || (reinterpret_cast<uintptr_t>(F_dev) % 8) != 0))
+    return fail(ctx, SC_ERR_INVALID_ARG, "F_dev NULL or misaligned");
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(ctx, SC_ERR_INVALID_ARG, "device ordinal beyond 63");
+  // the array's address in the current context (each context has its own copy)
   void *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_static_scratch);   // current device is `dev`
-      if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: cudaGetSymbolAddress");
-      g_scratch_addr[dev] = p;
-    }
-    scratch = g_scratch_addr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress(&scratch, g_static_scratch);
+  if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: cudaGetSymbolAddress");
 
   uint8_t *ws = static_cast<uint8_t *>(scratch);
   uint32_t *status = reinterpret_cast<uint32_t *>(ws + ctx->ws.status_off);
