@@ -46,3 +46,46 @@ def test_training_fits_a_smooth_target(dev):
     assert hist[-1] < 0.05 * hist[0]
     pred = net.predict(X)
     assert np.mean((pred - T) ** 2) < 0.01
+
+
+def test_adam_kernel_matches_fp64_reference(dev):
+    """sc_mlp_adam (FP32 on the GPU) against oracle.mlp.adam_step (FP64),
+    element by element over 12 steps of a seeded gradient sequence, with the
+    bias correction active (steps 1..12 of beta2 = 0.999 leave 1 - beta2^t far
+    from 1).  The oracle gets the hyperparameters the kernel receives (their
+    FP32 values), so only FP32 arithmetic separates the two.  Tolerances from
+    that arithmetic: the moments carry a few FP32 roundings per step relative
+    to |moment| + |g| (resp. v + g^2), at most t 2^-23 summed over t steps;
+    the step's bias corrections 1 - beta^t lose up to 2^-23 / (1 - beta2^t)
+    ~ 2^-17 to cancellation, so each update is good to lr 2^-12 at most,
+    and the stored params round by 2^-24 |p| per step."""
+    import ctypes
+    from paper_2509_21037_gb300.mlp import _lib
+    lib = _lib()
+    rng = np.random.default_rng(5)
+    n, K = 4099, 12                                # ragged against the 256-thread blocks
+    f32 = lambda x: float(np.float32(x))
+    lr, b1, b2, eps = f32(3e-3), f32(0.9), f32(0.999), f32(1e-8)
+    p0 = rng.standard_normal(n).astype(np.float32)
+    gs = [(rng.standard_normal(n) * np.exp(rng.uniform(-6, 3, n))).astype(np.float32) for _ in range(K)]
+    gs[0][:7] = 0.0                                # zero gradients: v = 0 there, eps guards the division
+    p = torch.from_numpy(p0.copy()).to(dev)
+    m = torch.zeros(n, dtype=torch.float32, device=dev)
+    v = torch.zeros_like(m)
+    pr, mr, vr = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    moved = np.zeros(n)
+    for t in range(1, K + 1):
+        g64 = gs[t - 1].astype(np.float64)
+        g = torch.from_numpy(gs[t - 1]).to(dev)
+        rc = lib.sc_mlp_adam(n, p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), ctypes.c_float(lr),
+                             ctypes.c_float(b1), ctypes.c_float(b2), ctypes.c_float(eps), t, None)
+        assert rc == 0
+        pn, mr, vr = om.adam_step(pr, g64, mr, vr, lr, b1, b2, eps, t)
+        moved += np.abs(pn - pr)
+        pr = pn
+        pg, mg, vg = (x.cpu().numpy().astype(np.float64) for x in (p, m, v))
+        assert np.all(np.abs(mg - mr) <= t * 2.0 ** -21 * (np.abs(mr) + np.abs(g64))), f"m at step {t}"
+        assert np.all(np.abs(vg - vr) <= t * 2.0 ** -21 * (vr + g64 ** 2)), f"v at step {t}"
+        assert np.all(np.abs(pg - pr) <= t * (2.0 ** -23 * np.abs(pr) + lr * 2.0 ** -12)), f"params at step {t}"
+    # the updates are large against the tolerance (the comparison is not vacuous)
+    assert np.median(moved) > 100 * K * lr * 2.0 ** -12
