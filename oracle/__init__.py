@@ -60,7 +60,7 @@ def regularize(K: sp.spmatrix, fixed: Sequence[int]) -> np.ndarray:
     nodes): rows and columns of the fixed dofs are zeroed, their diagonal set
     to 1.  For a minimal fixing set the free-free block of K_reg^{-1} is the
     fixing-node generalised inverse."""
-    A = np.asarray(K.todense(), dtype=np.float64).copy()
+    A = sp.csr_matrix(K).toarray().astype(np.float64, copy=False)   # a fresh dense array
     f = np.asarray(fixed, dtype=np.int64)
     A[f, :] = 0.0
     A[:, f] = 0.0
@@ -98,24 +98,28 @@ def _upper_solve_small(U: np.ndarray, R: np.ndarray) -> np.ndarray:
     return X
 
 
-def cholesky(A: np.ndarray, block: int = 64) -> np.ndarray:
-    """Blocked right-looking dense Cholesky: A = G G^T, G lower (FP64).
+def cholesky(A: np.ndarray, block: int = 128) -> np.ndarray:
+    """Blocked left-looking dense Cholesky: A = G G^T, G lower (FP64).
 
-    For each diagonal block: factor it, solve the panel below against it,
-    subtract the panel's outer product from the trailing matrix.
+    For each block column J (columns j0..j1) in turn: subtract the
+    contributions of the finished columns, A[j0:, J] -= G[j0:, :j0] G[J, :j0]^T
+    (one matrix product), factor the diagonal block, and solve the rows below
+    against it.  Only the lower triangle is read and written.
     """
     A = np.array(A, dtype=np.float64, copy=True)
     n = A.shape[0]
-    for k0 in range(0, n, block):
-        k1 = min(k0 + block, n)
-        Gkk = _cholesky_unblocked(A[k0:k1, k0:k1])
-        A[k0:k1, k0:k1] = Gkk
-        if k1 < n:
-            # panel P with P Gkk^T = A[k1:, k0:k1]  <=>  Gkk P^T = A[k1:, k0:k1]^T
-            P = _lower_solve_small(Gkk, A[k1:, k0:k1].T).T
-            A[k1:, k0:k1] = P
-            A[k1:, k1:] -= P @ P.T
-    return np.tril(A)
+    for j0 in range(0, n, block):
+        j1 = min(j0 + block, n)
+        if j0 > 0:
+            A[j0:, j0:j1] -= A[j0:, :j0] @ A[j0:j1, :j0].T
+        Gjj = _cholesky_unblocked(A[j0:j1, j0:j1])
+        A[j0:j1, j0:j1] = Gjj
+        if j1 < n:
+            # panel P with P Gjj^T = A[j1:, J]  <=>  Gjj P^T = A[j1:, J]^T
+            A[j1:, j0:j1] = _lower_solve_small(Gjj, A[j1:, j0:j1].T).T
+    for i in range(n - 1):                       # G = lower triangle (in place: no second n x n copy)
+        A[i, i + 1:] = 0.0
+    return A
 
 
 def forward_substitution(G: np.ndarray, R: np.ndarray, block: int = 64) -> np.ndarray:
@@ -183,9 +187,10 @@ def regularized_sparse(K: sp.spmatrix, fixed: Sequence[int]) -> sp.csr_matrix:
     return A.tocsr()
 
 
-def residual(A: sp.csr_matrix, X: np.ndarray, R0: np.ndarray) -> np.ndarray:
+def residual_numpy(A: sp.csr_matrix, X: np.ndarray, R0: np.ndarray) -> np.ndarray:
     """R0 - A X with every product and sum carried in double-double, rounded
-    once at the end (A sparse)."""
+    once at the end (A sparse): per row, the stored entries in storage order,
+    hi <- TwoSum(hi, p), lo <- lo + (sum error + product error)."""
     A = sp.csr_matrix(A)
     hi = np.array(R0, dtype=np.float64, copy=True)
     lo = np.zeros_like(hi)
@@ -199,6 +204,69 @@ def residual(A: sp.csr_matrix, X: np.ndarray, R0: np.ndarray) -> np.ndarray:
         hi[rows] = s
         lo[rows] += se + pe
     return hi + lo
+
+
+_C_LIB = None
+
+
+def _c_residual_lib():
+    """oracle/residual.c (the loops of ``residual_numpy``), compiled once with
+    gcc into oracle/_build/ (OpenMP, no fused multiply-adds); None if no C
+    compiler is available."""
+    global _C_LIB
+    if _C_LIB is not None:
+        return _C_LIB or None
+    import ctypes
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "residual.c")
+    out_dir = os.path.join(here, "_build")
+    so = os.path.join(out_dir, "liboracle_residual.so")
+    try:
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            os.makedirs(out_dir, exist_ok=True)
+            tmp = so + ".%d.tmp" % os.getpid()
+            subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                            src, "-o", tmp], check=True, capture_output=True)
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        vp = ctypes.c_void_p
+        lib.oracle_residual.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp]
+        lib.oracle_residual.restype = None
+        _C_LIB = lib
+    except (OSError, subprocess.CalledProcessError):
+        _C_LIB = False
+    return _C_LIB or None
+
+
+def build_c() -> bool:
+    """Compile the oracle's C part (``residual.c``); True when it is usable."""
+    return _c_residual_lib() is not None
+
+
+def residual(A: sp.csr_matrix, X: np.ndarray, R0: np.ndarray) -> np.ndarray:
+    """R0 - A X, error-free until one final rounding (see ``residual_numpy``);
+    the same loops in C (oracle/residual.c, bit-identical results) when a C
+    compiler is available, else the numpy form."""
+    lib = _c_residual_lib()
+    if lib is None:
+        return residual_numpy(A, X, R0)
+    A = sp.csr_matrix(A)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    R0 = np.ascontiguousarray(R0, dtype=np.float64)
+    squeeze = X.ndim == 1
+    if squeeze:
+        X = X[:, None]
+        R0 = R0[:, None]
+    indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(A.indices, dtype=np.int64)
+    data = np.ascontiguousarray(A.data, dtype=np.float64)
+    out = np.empty((A.shape[0], X.shape[1]))
+    lo = np.empty_like(out)
+    lib.oracle_residual(A.shape[0], X.shape[1], indptr.ctypes.data, indices.ctypes.data, data.ctypes.data,
+                        X.ctypes.data, R0.ctypes.data, out.ctypes.data, lo.ctypes.data)
+    return out[:, 0] if squeeze else out
 
 
 class _Memo:

@@ -299,3 +299,18 @@ def test_config1_anchor_golden():
     assert abs(got["trace"] - 266.3118) < 5e-5
     assert abs(got["lambda_min"] - 0.5774) < 5e-5
     assert abs(got["lambda_max"] - 173.8) < 5e-2
+
+
+def test_residual_c_and_numpy_forms_bit_identical():
+    """oracle/residual.c runs the loops of residual_numpy; on inputs spanning
+    16 decades the two agree bit for bit (and the numpy form is the one the
+    rational-arithmetic pin above also checks through this equality)."""
+    if not oracle.build_c():
+        pytest.skip("no C compiler")
+    rng = np.random.default_rng(9)
+    A = sp.random(400, 400, density=0.03, random_state=4, format="csr") + sp.eye(400)
+    A.data = rng.standard_normal(A.nnz) * 10.0 ** rng.integers(-8, 8, A.nnz)
+    X = rng.standard_normal((400, 7)) * 10.0 ** rng.integers(-8, 8, (400, 7))
+    R0 = rng.standard_normal((400, 7))
+    assert np.array_equal(oracle.residual(A, X, R0), oracle.residual_numpy(A, X, R0))
+    assert np.array_equal(oracle.residual(A, X[:, 0], R0[:, 0]), oracle.residual_numpy(A, X[:, :1], R0[:, :1])[:, 0])
