@@ -63,7 +63,7 @@ typedef enum {
   SC_ERR_NOT_SPD = 2,     /* a diagonal entry of L is not positive and finite */
   SC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has details) */
   SC_ERR_OOM = 4,         /* a buffer passed is smaller than sc_get_sizes asks */
-  SC_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (reserved) */
+  SC_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (sc_options.poll_limit) */
   SC_ERR_INTERNAL = 6,
   SC_ERR_STATE = 7        /* call out of order (e.g. assemble before upload) */
 } sc_status;
@@ -122,14 +122,33 @@ enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
  *            (largest first) from an atomic counter in the workspace status
  *            area until the list is exhausted (a persistent work queue; no
  *            CTA waits on another). */
+/* tile:     SYRK output tile of the split-precision subdomains: SC_TILE_32
+ *            (default) -- 32x32 blocks of F on the warp-level tensor-core
+ *            instruction (mma.sync); SC_TILE_TC128 -- 128x32 tiles (four row
+ *            chunks by one column chunk, summed over the union of the four
+ *            chunk pairs' supernode blocks) on the fifth-generation tensor
+ *            cores (tcgen05.mma, accumulators in tensor memory).  Ignored for
+ *            FP64 subdomains.  Same digits, same error bound.
+ * sub_tile:  optional per-subdomain tile (nsub entries, host, read during
+ *            sc_plan, 0 or 1); overrides `tile`.  Together with sub_slices it
+ *            is the per-subdomain variant the autotuner and the learned
+ *            selector choose (sc_select).
+ * poll_limit: number of polls of every bounded device-side wait (the tcgen05
+ *            kernels wait on mbarriers for their tensor-core work) before the
+ *            kernel gives up, sets the timeout bit of the status word and
+ *            returns (sc_device_status: SC_ERR_TIMEOUT); 0 selects 2^26. */
 typedef struct {
   int32_t precision;
   int32_t n_slices;
   const int8_t *sub_slices;
   int64_t ws_limit;
   int32_t persistent;
-  int32_t reserved; /* must be zero */
+  int32_t tile;
+  const int8_t *sub_tile;
+  int64_t poll_limit;
 } sc_options;
+
+enum { SC_TILE_32 = 0, SC_TILE_TC128 = 1 };
 
 typedef struct {
   size_t plan_bytes;       /* device plan tables (sc_upload_plan) */
@@ -224,7 +243,8 @@ sc_status sc_assemble_batch(sc_ctx *ctx, const double *L_values_dev, double *F_d
 sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_values_dev, double *F_dev, void *stream);
 
 /* Synchronises `stream` and reads the device status word in ws_dev:
- * SC_OK, or SC_ERR_NOT_SPD when a diagonal of L was not positive and finite. */
+ * SC_OK, SC_ERR_NOT_SPD when a diagonal of L was not positive and finite, or
+ * SC_ERR_TIMEOUT when a bounded device wait gave up (F is then undefined). */
 sc_status sc_device_status(sc_ctx *ctx, const void *ws_dev, void *stream);
 
 /* ---- solution ------------------------------------------------------------------ */
@@ -252,6 +272,47 @@ sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_
  * with leading dimension ld >= m_i.  Asynchronous on `stream`. */
 sc_status sc_export_F(sc_ctx *ctx, const double *F_dev, int32_t i, double *dst_dev, int32_t ld,
                       void *stream);
+
+/* ---- learned variant choice (row a9 of the hot path; no counterpart in the paper) -- */
+
+/* Features of every subdomain, from the plan (host, exact counters): log2 of
+ * n, m, nnz(L), active supernodes, the largest active supernode, the useful
+ * TRSM flops, the useful SYRK flops, the dense-equivalent flops and the
+ * doubles of the sparse Y, and log2(max / min diagonal entry of L) when
+ * L_values_host (the concatenated values, host) is given, else 0.
+ * out: nsub x SC_NUM_FEATURES floats, row-major. */
+#define SC_NUM_FEATURES 10
+sc_status sc_subdomain_features(const sc_ctx *ctx, const double *L_values_host, float *out);
+
+/* A trained variant predictor: the MLP of include/sc_mlp.h with
+ * n_in = SC_NUM_FEATURES, n_out = n_variants + (number of split variants),
+ * whose outputs (after y = y' * y_scale + y_shift) are the log10 time of every
+ * variant and then the log10 relative error of every split variant, in
+ * variant order; inputs are normalised as x' = (x - x_shift) / x_scale.
+ * A variant is (slices[v], tiles[v]): 0 = FP64 (tile SC_TILE_32), or 3..7
+ * digits with SC_TILE_32 or SC_TILE_TC128 (sc_options).  The FP64 variant must
+ * be one of them.  params_dev is device memory; the other arrays are host. */
+typedef struct {
+  int32_t n_variants;
+  const int8_t *slices;
+  const int8_t *tiles;
+  int32_t n_hidden;
+  const float *params_dev;
+  const float *x_shift, *x_scale;
+  const float *y_shift, *y_scale;
+} sc_selector;
+
+/* Device workspace of sc_select, in floats. */
+sc_status sc_select_workspace(const sc_ctx *ctx, const sc_selector *sel, size_t *ws_floats);
+
+/* Per subdomain of the planned batch, the fastest variant whose predicted
+ * error times `margin` (>= 1) meets `tol`, the FP64 variant qualifying always:
+ * the features of sc_subdomain_features, one MLP forward pass over the batch
+ * on the GPU (sc_mlp_forward, ws_dev caller-owned), the choice on the host.
+ * Writes sub_slices and sub_tile (nsub entries each, host) for the
+ * sc_options of the plan that then runs the batch.  Synchronises `stream`. */
+sc_status sc_select(sc_ctx *ctx, const sc_selector *sel, const double *L_values_host, double tol, double margin,
+                    float *ws_dev, size_t ws_floats, int8_t *sub_slices, int8_t *sub_tile, void *stream);
 
 /* ---- misc ---------------------------------------------------------------------- */
 

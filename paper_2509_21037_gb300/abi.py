@@ -1,4 +1,5 @@
-"""ctypes mirror of include/sc.h, include/sc_implicit.h and include/sc_dense.h (argument marshalling only)."""
+"""ctypes mirror of include/sc.h, include/sc_implicit.h, include/sc_probe.h, include/sc_pipeline.h and
+include/sc_dense.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -23,9 +24,12 @@ class SubdomainDesc(ctypes.Structure):
 SC_FP64, SC_SPLIT_BF16 = 0, 1
 
 
+SC_TILE_32, SC_TILE_TC128 = 0, 1
+
+
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("n_slices", c_i32), ("sub_slices", c_vp), ("ws_limit", c_i64),
-                ("persistent", c_i32), ("reserved", c_i32)]
+                ("persistent", c_i32), ("tile", c_i32), ("sub_tile", c_vp), ("poll_limit", c_i64)]
 
 
 class Sizes(ctypes.Structure):
@@ -40,6 +44,14 @@ class Stats(ctypes.Structure):
                 ("bytes_apply", ctypes.c_double), ("n_supernodes", c_i64), ("n_trsm_tasks", c_i64),
                 ("n_syrk_tasks", c_i64), ("n_apply_tasks", c_i64), ("y_doubles", c_i64),
                 ("max_supernode", c_i64), ("n_waves", c_i64)]
+
+
+SC_NUM_FEATURES = 10
+
+
+class Selector(ctypes.Structure):
+    _fields_ = [("n_variants", c_i32), ("slices", c_vp), ("tiles", c_vp), ("n_hidden", c_i32),
+                ("params_dev", c_vp), ("x_shift", c_vp), ("x_scale", c_vp), ("y_shift", c_vp), ("y_scale", c_vp)]
 
 
 # every symbol include/sc.h declares, with (argtypes, restype)
@@ -59,6 +71,10 @@ SC_SYMBOLS = {
     "sc_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), c_i32], c_int),
     "sc_export_plan": ([c_vp, c_vp, c_sz], c_int),
     "sc_workspace_layout": ([c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_subdomain_features": ([c_vp, c_vp, c_vp], c_int),
+    "sc_select_workspace": ([c_vp, ctypes.POINTER(Selector), ctypes.POINTER(c_sz)], c_int),
+    "sc_select": ([c_vp, ctypes.POINTER(Selector), c_vp, ctypes.c_double, ctypes.c_double, c_vp, c_sz, c_vp, c_vp,
+                   c_vp], c_int),
     "sc_last_error": ([c_vp], ctypes.c_char_p),
     "sc_destroy": ([c_vp], None),
 }
@@ -110,6 +126,12 @@ PIPELINE_SYMBOLS = {
     "scp_destroy": ([c_vp], None),
 }
 
+# every symbol include/sc_probe.h declares
+PROBE_SYMBOLS = {
+    "sc_probe_fp64_fma": ([c_i32, c_i32, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_i64), c_vp],
+                          c_int),
+}
+
 DENSE_SYMBOLS = {
     "scd_create": ([ctypes.POINTER(c_vp), c_i32], c_int),
     "scd_trsm_syrk": ([c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
@@ -127,6 +149,7 @@ def _declare(lib, table):
 def declare(lib):
     _declare(lib, SC_SYMBOLS)
     _declare(lib, IMPLICIT_SYMBOLS)
+    _declare(lib, PROBE_SYMBOLS)
 
 
 def declare_pipeline(lib):

@@ -42,7 +42,7 @@ sc_ctx::~sc_ctx() {
 
 std::vector<int> sc_ctx::groups(int w) const {
   std::vector<int> g;
-  for (int v = 0; v < 8; ++v)
+  for (int v = 0; v < kNumVariants; ++v)
     if (waves[w].trsm[v][1] > 0 || waves[w].syrk[v][1] > 0) g.push_back(v);
   return g;
 }
@@ -185,7 +185,9 @@ sc_status sc_device_status(sc_ctx *ctx, const void *ws_dev, void *stream) {
   uint32_t h = 0;
   e = cudaMemcpy(&h, static_cast<const uint8_t *>(ws_dev) + ctx->ws.status_off, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sc_device_status read");
-  if (h & 1u) return fail(ctx, SC_ERR_NOT_SPD, "a diagonal entry of L is not positive and finite");
+  if (h & kStatusNotSpd) return fail(ctx, SC_ERR_NOT_SPD, "a diagonal entry of L is not positive and finite");
+  if (h & kStatusTimeout)
+    return fail(ctx, SC_ERR_TIMEOUT, "a bounded device wait gave up (sc_options.poll_limit polls)");
   if (h) return fail(ctx, SC_ERR_INTERNAL, "unknown device status bits");
   return SC_OK;
 }

@@ -26,6 +26,16 @@ constexpr int kChunk = 32;      // column chunk width of the TRSM / SYRK tasks
 constexpr int kTile = 32;       // F tile edge
 constexpr int kThreads = 128;   // threads per CTA of the assembly kernels
 
+// bits of the workspace status word
+enum : uint32_t { kStatusNotSpd = 1u, kStatusTimeout = 2u };
+
+// Per-subdomain kernel variant: 0 = FP64; S (3..7) = split precision with S
+// digits and 32x32 SYRK blocks (mma.sync); kVarTile | S = the same digits
+// with 128x32 SYRK tiles on tcgen05.  One launch group per variant.
+constexpr int kVarTile = 8;
+constexpr int kNumVariants = 16;
+inline int var_digits(int v) { return v & 7; }
+
 struct SubDev {
   int64_t F_off;     // doubles, start of F_i (tile-packed lower)
   int64_t L_off;     // start of L_i's values in the concatenated value array
@@ -57,9 +67,13 @@ struct TrsmTask {
   int32_t pad;
 };
 
+// A 32x32 block of F (sorted chunks q1 >= q2, supernodes active on both), or
+// for a tcgen05 variant a 128x32 tile: rows = chunks q1 .. q1 + 3 (q1 a
+// multiple of 4), columns = chunk q2, supernodes = the union over its chunk
+// pairs on or below the diagonal.
 struct SyrkTask {
-  int32_t sub, q1, q2;        // output block of sorted chunks q1 >= q2
-  int32_t list_off, list_len; // supernodes active on both chunks
+  int32_t sub, q1, q2;
+  int32_t list_off, list_len;
   int32_t pad[3];
 };
 
@@ -114,6 +128,12 @@ struct Section {
   size_t off = 0, bytes = 0;
 };
 
+// Per-subdomain plan counters, the structural features of the learned variant
+// choice (sc_subdomain_features).
+struct SubFeat {
+  double n, m, nnzL, supernodes, max_supernode, flops_trsm, flops_syrk, flops_dense, y_doubles;
+};
+
 // First kHeaderBytes (512) bytes of the plan blob: a self-describing header, so that the
 // host copy (sc_export_plan) can be inspected or stored.  Sections follow in
 // the order of the arrays below, each 256-byte aligned.
@@ -148,12 +168,13 @@ struct sc_ctx {
   std::string err;
   int32_t precision = SC_FP64;       // SC_SPLIT_BF16 when any subdomain runs split
   int32_t n_slices = 0;              // largest digit count of any subdomain (plane sizing)
-  std::vector<int8_t> sub_var;       // per subdomain: 0 = FP64, 3..7 = split digits
+  std::vector<int8_t> sub_var;       // per subdomain: 0 = FP64, 3..7 = split digits, kVarTile | S = tcgen05 SYRK
+  int64_t poll_limit = 0;            // polls of a bounded device wait (0 = default)
   int64_t ws_limit = 0;              // workspace bytes per wave (0 = one wave)
   int32_t persistent = 0;            // FP64 TRSM/SYRK as work-queue kernels (sc_options.persistent)
   // per wave, launch groups by variant (index 0 = FP64, 3..7 = digits): first item, count
   struct WaveGroups {
-    int64_t trsm[8][2] = {}, syrk[8][2] = {}, sblk[8][2] = {};
+    int64_t trsm[sc::kNumVariants][2] = {}, syrk[sc::kNumVariants][2] = {}, sblk[sc::kNumVariants][2] = {};
   };
   std::vector<WaveGroups> waves;
   std::vector<int32_t> sub_wave;     // wave of every subdomain
@@ -164,6 +185,8 @@ struct sc_ctx {
       s_perm, s_lambda, s_apply, s_active, s_cuts, s_sblk;
   int64_t n_sns = 0, n_trsm = 0, n_syrk = 0, n_apply = 0, n_cols = 0, n_active_cols = 0, n_sblk = 0;
   std::vector<int64_t> F_offsets, L_offsets;
+  std::vector<sc::SubFeat> sub_feat;    // per subdomain, in batch order
+  std::vector<int64_t> diag_index;      // per column of every subdomain: index of L(c, c) in the values
   std::vector<int32_t> n, m;
   sc::WsLayout ws;
   sc_sizes sizes{};
@@ -174,8 +197,8 @@ struct sc_ctx {
   void *stage_events[4] = {nullptr, nullptr, nullptr, nullptr};  // cudaEvent_t, stage timing
   bool stage_recorded = false;
   // created on first use by a batch with several variant groups
-  void *aux_streams[8] = {}, *aux_done[8] = {}, *fork_event = nullptr;
-  std::vector<int> groups(int w) const;   // variants present in wave w (0 = FP64, 3..7)
+  void *aux_streams[sc::kNumVariants] = {}, *aux_done[sc::kNumVariants] = {}, *fork_event = nullptr;
+  std::vector<int> groups(int w) const;   // variants present in wave w
   ~sc_ctx();
 
   sc::PlanPtrs ptrs() const;
@@ -204,6 +227,9 @@ int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream);
 int launch_yslice_group(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Y, void *ws,
                         void *stream);
 int launch_syrk_split(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
+// the 128x32-tile SYRK on tcgen05 (sc_syrk_tc.cu); tc_smem_bytes: its dynamic shared memory
+int launch_syrk_tc(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
+int tc_smem_bytes(int S);
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream);
 int launch_export(const sc_ctx &c, const double *F, int32_t i, double *dst, int32_t ld, void *stream);
 

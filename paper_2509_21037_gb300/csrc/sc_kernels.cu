@@ -37,8 +37,6 @@
 
 namespace sc {
 
-enum : uint32_t { kStatusNotSpd = 1u };
-
 __global__ void prep_kernel(const int64_t *__restrict__ lcp, const int32_t *__restrict__ active,
                             int64_t nact, const double *__restrict__ Lv, double *__restrict__ invd,
                             uint32_t *__restrict__ status) {
@@ -74,9 +72,10 @@ __global__ void fpad_kernel(const SubDev *__restrict__ subs, double *__restrict_
 
 // One TRSM task (a 32-column chunk of one subdomain).  Xs: the current 32-row
 // block of the solved chunk, [row][column]; cps[q] = index of L(p, c0+kb+q) minus p.
+// The diagonal triangles are solved by warp `tri` of the CTA (see tri_warp).
 __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, const double *__restrict__ Lv,
                                           const double *__restrict__ invd, double *__restrict__ Y,
-                                          double (*Xs)[33], int64_t *cps) {
+                                          double (*Xs)[33], int64_t *cps, int tri) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c_hi = t.c_lo + t.w;
 
@@ -112,7 +111,7 @@ __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, c
       // columns at or after the block's cut are still zero in these rows
       const int wk = min(b, P.cuts[s.cut_off + (kb >> 5)]) - a;
       if (wk <= 0) continue;
-      if (warp == 0) {
+      if (warp == tri) {
         if (lane < kw) cps[lane] = cp[kb + lane] - (kb + lane);
         __syncwarp();
         if (lane < wk) {
@@ -127,20 +126,32 @@ __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, c
         }
       }
       __syncthreads();
-      if (lane < wk) {
-        for (int p = kb + kw + warp; p < nrow; p += kThreads / 32) {
+      // Update of the rows below.  The FP64 pipe charges a warp instruction in
+      // full whatever the number of active lanes, so a column range narrower
+      // than 32 is packed: lane groups of W >= wk lanes (a power of two) take
+      // 32 / W rows per warp step.
+      const int W = wk <= 4 ? 4 : wk <= 8 ? 8 : wk <= 16 ? 16 : 32;
+      const int R = 32 / W, cl = lane & (W - 1), ro = lane / W;
+      if (cl < wk) {
+        for (int p = kb + kw + warp * R + ro; p < nrow; p += (kThreads / 32) * R) {
           // the target row is the accumulator: no separate subtraction on the FP64 pipe
           double *tg = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
-          double acc = tg[lane];
+          double acc = tg[cl];
 #pragma unroll 8
-          for (int q = 0; q < kw; ++q) acc = fma(-Lv[cps[q] + p], Xs[q][lane], acc);
-          tg[lane] = acc;
+          for (int q = 0; q < kw; ++q) acc = fma(-Lv[cps[q] + p], Xs[q][cl], acc);
+          tg[cl] = acc;
         }
       }
       __syncthreads();
     }
   }
 }
+
+// The warp of a CTA that solves the serial 32x32 triangles.  The FP64 pipe
+// belongs to the SM's four sub-partitions and a CTA's warps are spread over
+// them, so a fixed choice (warp 0) would put the triangle work of every
+// co-resident CTA on one sub-partition; a hash of the task index spreads it.
+__device__ __forceinline__ int tri_warp(unsigned k) { return (int)((k * 2654435761u) >> 30); }
 
 // Work-queue form (queue != nullptr): a grid sized to the resident CTAs pulls
 // task indices from an atomic counter until the list is exhausted; otherwise
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const 
   __shared__ int64_t cps[32];
   __shared__ int next;
   if (!queue) {
-    trsm_task(P, P.trsm_tasks[blockIdx.x], Lv, invd, Y, Xs, cps);
+    trsm_task(P, P.trsm_tasks[blockIdx.x], Lv, invd, Y, Xs, cps, tri_warp(blockIdx.x));
     return;
   }
   for (;;) {
@@ -161,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const 
     const int k = next;
     __syncthreads();
     if (k >= ntask) break;
-    trsm_task(P, P.trsm_tasks[k], Lv, invd, Y, Xs, cps);
+    trsm_task(P, P.trsm_tasks[k], Lv, invd, Y, Xs, cps, tri_warp((unsigned)k));
     __syncthreads();
   }
 }
@@ -406,8 +417,9 @@ int launch_group_trsm(const sc_ctx &c, int w, int v, const double *Lv, const dou
     }
     return (int)cudaGetLastError();
   }
-  int e = launch_lpack_split(c, v, G.sblk[v][0], G.sblk[v][1], Lv, ws, stream);
-  if (!e) e = launch_trsm_split(c, v, G.trsm[v][0], G.trsm[v][1], Lv, invd, ws, Y, stream);
+  const int S = var_digits(v);
+  int e = launch_lpack_split(c, S, G.sblk[v][0], G.sblk[v][1], Lv, ws, stream);
+  if (!e) e = launch_trsm_split(c, S, G.trsm[v][0], G.trsm[v][1], Lv, invd, ws, Y, stream);
   return e;
 }
 
@@ -431,9 +443,11 @@ int launch_group_syrk(const sc_ctx &c, int w, int v, const double *Y, void *ws, 
     }
     return (int)cudaGetLastError();
   }
-  int e = launch_yslice_group(c, v, G.sblk[v][0], G.sblk[v][1], Y, ws, stream);
-  if (!e) e = launch_syrk_split(c, v, G.syrk[v][0], G.syrk[v][1], ws, F, stream);
-  return e;
+  const int S = var_digits(v);
+  int e = launch_yslice_group(c, S, G.sblk[v][0], G.sblk[v][1], Y, ws, stream);
+  if (e) return e;
+  if (v & kVarTile) return launch_syrk_tc(c, S, G.syrk[v][0], G.syrk[v][1], ws, F, stream);
+  return launch_syrk_split(c, S, G.syrk[v][0], G.syrk[v][1], ws, F, stream);
 }
 
 int launch_apply(const sc_ctx &c, const double *F, const double *lam, double *q, void *stream) {

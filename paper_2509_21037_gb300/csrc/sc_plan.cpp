@@ -242,7 +242,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   std::vector<ApplyTask> apply;
   std::vector<int32_t> active_cols;
   std::vector<int32_t> cuts;
-  std::vector<int32_t> sblk_v[8], sblk_w[8];
+  std::vector<int32_t> sblk_v[kNumVariants], sblk_w[kNumVariants];
   std::vector<double> trsm_cost, syrk_cost;
   std::vector<int8_t> trsm_var, syrk_var;
   std::vector<int32_t> trsm_wave, syrk_wave;
@@ -298,6 +298,8 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     ctx->n[i] = n;
     ctx->m[i] = m;
     max_m = std::max(max_m, m);
+    const sc_stats st0 = st;                      // per-subdomain counters: differences at the end
+    const int64_t y0 = y_all + y_total, nsn0 = (int64_t)sns.size();
     SubDev sd{};
     sd.F_off = ctx->F_offsets[i];
     sd.L_off = ctx->L_offsets[i];
@@ -423,8 +425,43 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       trsm_var.push_back(ctx->sub_var[i]);
       trsm_wave.push_back(ctx->sub_wave[i]);
     }
+    // 128x32 tiles for the tcgen05 SYRK: rows = chunks q1 .. q1 + 3 (q1 = 4 Q), columns = chunk q2;
+    // supernodes = the union of the chunk pairs' common lists (lower triangle only)
+    for (int32_t q1 = 0; (ctx->sub_var[i] & kVarTile) && q1 < nchunk; q1 += 4) {
+      for (int32_t q2 = 0; q2 <= std::min(q1 + 3, nchunk - 1); ++q2) {
+        SyrkTask t{};
+        t.sub = i; t.q1 = q1; t.q2 = q2;
+        t.list_off = (int32_t)syrk_list.size();
+        std::vector<int32_t> uni;
+        for (int32_t qa = std::max(q1, q2); qa <= std::min(q1 + 3, nchunk - 1); ++qa) {
+          const auto &A = clist[qa], &B = clist[q2];
+          size_t ia = 0, ib = 0;
+          while (ia < A.size() && ib < B.size()) {
+            if (A[ia] < B[ib]) ++ia;
+            else if (B[ib] < A[ia]) ++ib;
+            else { uni.push_back(A[ia]); ++ia; ++ib; }
+          }
+        }
+        std::sort(uni.begin(), uni.end());
+        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+        double exec = 0;
+        const int32_t j1min = std::max(q1, q2) * kChunk;
+        for (int32_t s : uni) {
+          const SnDev &sn = sns[gidx[s]];
+          syrk_list.push_back(gidx[s]);
+          for (int32_t k0 = 0; k0 < sn.ns; k0 += 32)
+            if (j1min < cuts[sn.cut_off + k0 / 32]) exec += 2.0 * 128 * kChunk * 32;
+        }
+        t.list_len = (int32_t)syrk_list.size() - t.list_off;
+        st.flops_syrk_exec += exec;
+        syrk.push_back(t);
+        syrk_cost.push_back(exec + 1e3 * (t.list_len + 1));
+        syrk_var.push_back(ctx->sub_var[i]);
+        syrk_wave.push_back(ctx->sub_wave[i]);
+      }
+    }
     // chunk-pair lists (lower triangle of sorted chunks)
-    for (int32_t q1 = 0; q1 < nchunk; ++q1) {
+    for (int32_t q1 = 0; !(ctx->sub_var[i] & kVarTile) && q1 < nchunk; ++q1) {
       for (int32_t q2 = 0; q2 <= q1; ++q2) {
         SyrkTask t{};
         t.sub = i; t.q1 = q1; t.q2 = q2;
@@ -464,6 +501,18 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
     st.flops_dense += (double)n * n * m + (double)n * m * (m + 1.0);
     st.bytes_assembly += 12.0 * (n > 0 ? (double)D.L_colptr[n] : 0.0) + 8.0 * m * (m + 1.0) / 2.0;
     st.bytes_apply += 8.0 * m * (m + 1.0) / 2.0 + 16.0 * m;
+    {
+      SubFeat f{};
+      f.n = n; f.m = m;
+      f.nnzL = n > 0 ? (double)D.L_colptr[n] : 0.0;
+      f.supernodes = (double)((int64_t)sns.size() - nsn0);
+      for (int64_t k = nsn0; k < (int64_t)sns.size(); ++k) f.max_supernode = std::max(f.max_supernode, (double)sns[k].ns);
+      f.flops_trsm = st.flops_trsm - st0.flops_trsm;
+      f.flops_syrk = st.flops_syrk - st0.flops_syrk;
+      f.flops_dense = st.flops_dense - st0.flops_dense;
+      f.y_doubles = (double)(y_all + y_total - y0);
+      ctx->sub_feat.push_back(f);
+    }
     col_total += m;
     lcp_total += n;
   }
@@ -504,7 +553,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   }
   std::vector<int32_t> sblk;
   for (size_t w = 0; w < ctx->waves.size(); ++w) {
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < kNumVariants; ++v) {
       auto &g = ctx->waves[w].sblk[v];
       g[0] = (int64_t)sblk.size() / 2;
       for (size_t k = 0; k < sblk_w[v].size(); ++k) {
@@ -515,6 +564,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
       g[1] = (int64_t)sblk.size() / 2 - g[0];
     }
   }
+  ctx->diag_index = lcp;
   ctx->blob.assign(kHeaderBytes, 0);
   add_section(ctx->blob, ctx->s_subs, subs);
   add_section(ctx->blob, ctx->s_sns, sns);
@@ -636,7 +686,19 @@ sc_status sc_plan(sc_ctx **out, int32_t nsub, const sc_subdomain_desc *subdomain
       }
       ctx->sub_var[i] = v;
     }
-    for (int8_t v : ctx->sub_var) ctx->n_slices = std::max<int32_t>(ctx->n_slices, v);
+    if (st == SC_OK && opt && opt->tile != SC_TILE_32 && opt->tile != SC_TILE_TC128)
+      st = fail(ctx, SC_ERR_INVALID_ARG, "tile must be SC_TILE_32 or SC_TILE_TC128");
+    for (int32_t i = 0; i < nsub && st == SC_OK && opt; ++i) {
+      const int tile = opt->sub_tile ? opt->sub_tile[i] : opt->tile;
+      if (tile != SC_TILE_32 && tile != SC_TILE_TC128) {
+        st = fail(ctx, SC_ERR_INVALID_ARG, "sub_tile entries must be 0 or 1");
+        break;
+      }
+      if (tile == SC_TILE_TC128 && ctx->sub_var[i] != 0) ctx->sub_var[i] = (int8_t)(ctx->sub_var[i] | kVarTile);
+    }
+    if (st == SC_OK && opt && opt->poll_limit < 0) st = fail(ctx, SC_ERR_INVALID_ARG, "poll_limit < 0");
+    ctx->poll_limit = opt ? opt->poll_limit : 0;
+    for (int8_t v : ctx->sub_var) ctx->n_slices = std::max<int32_t>(ctx->n_slices, var_digits(v));
     ctx->precision = ctx->n_slices > 0 ? SC_SPLIT_BF16 : SC_FP64;
     if (opt && opt->ws_limit < 0) st = fail(ctx, SC_ERR_INVALID_ARG, "ws_limit < 0");
     ctx->ws_limit = opt ? opt->ws_limit : 0;

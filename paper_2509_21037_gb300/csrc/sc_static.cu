@@ -77,7 +77,9 @@ extern "C" sc_status sc_assemble_batch_static(sc_ctx *ctx, const double *L_value
   e = cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return static_fail(ctx, e, "sc_assemble_batch_static: status read");
-  if (h & 1u) return fail(ctx, SC_ERR_NOT_SPD, "a diagonal entry of L is not positive and finite");
+  if (h & kStatusNotSpd) return fail(ctx, SC_ERR_NOT_SPD, "a diagonal entry of L is not positive and finite");
+  if (h & kStatusTimeout)
+    return fail(ctx, SC_ERR_TIMEOUT, "a bounded device wait gave up (sc_options.poll_limit polls)");
   if (h) return fail(ctx, SC_ERR_INTERNAL, "unknown device status bits");
   return SC_OK;
 }

@@ -35,7 +35,8 @@ class Plan:
     """
 
     def __init__(self, subdomains: Sequence, n_dual: int, precision: int = abi.SC_FP64, n_slices: int = 0,
-                 sub_slices: Optional[Sequence[int]] = None, ws_limit: int = 0, persistent: bool = False):
+                 sub_slices: Optional[Sequence[int]] = None, ws_limit: int = 0, persistent: bool = False,
+                 tile: int = abi.SC_TILE_32, sub_tile: Optional[Sequence[int]] = None, poll_limit: int = 0):
         self.lib = _native.sc_lib()
         self.nsub = len(subdomains)
         self.n_dual = int(n_dual)
@@ -56,10 +57,16 @@ class Plan:
         opt.n_slices = n_slices
         opt.ws_limit = int(ws_limit)
         opt.persistent = int(bool(persistent))
+        opt.tile = int(tile)
+        opt.poll_limit = int(poll_limit)
         if sub_slices is not None:
             self._sub_slices = np.ascontiguousarray(np.asarray(sub_slices), dtype=np.int8)
             assert len(self._sub_slices) == self.nsub
             opt.sub_slices = self._sub_slices.ctypes.data
+        if sub_tile is not None:
+            self._sub_tile = np.ascontiguousarray(np.asarray(sub_tile), dtype=np.int8)
+            assert len(self._sub_tile) == self.nsub
+            opt.sub_tile = self._sub_tile.ctypes.data
         st = self.lib.sc_plan(ctypes.byref(h), self.nsub, descs, self.n_dual, ctypes.byref(opt))
         self.h = h
         if st != abi.SC_OK:

@@ -47,7 +47,7 @@ def export_plan(plan) -> dict:
     return out
 
 
-def check_bounds(T: dict, sizes, stats) -> None:
+def check_bounds(T: dict, sizes, stats, tile_subs=()) -> None:
     """Every address the kernels form, against the buffer it indexes."""
     subs, sns = T["subs"], T["sns"]
     ncols = int(T["header"]["n_cols"])
@@ -97,7 +97,10 @@ def check_bounds(T: dict, sizes, stats) -> None:
             assert max(s["jlo"], t["c_lo"]) < min(s["jhi"], t["c_lo"] + t["w"])
     for t in T["syrk"]:
         sd = subs[t["sub"]]
-        assert 0 <= t["q2"] <= t["q1"] < sd["nt"]
+        if int(t["sub"]) in tile_subs:        # 128x32 tile: rows q1..q1+3 (q1 % 4 == 0), column chunk q2
+            assert t["q1"] % 4 == 0 and 0 <= t["q2"] <= min(t["q1"] + 3, sd["nt"] - 1) and t["q1"] < sd["nt"]
+        else:
+            assert 0 <= t["q2"] <= t["q1"] < sd["nt"]
         lst = T["syrk_list"][t["list_off"]:t["list_off"] + t["list_len"]]
         assert len(lst) == t["list_len"]
     for sd in subs:
@@ -108,8 +111,44 @@ def check_bounds(T: dict, sizes, stats) -> None:
     assert len(T["active"]) == 0 or (T["active"].min() >= 0 and T["active"].max() < ncols)
 
 
-def emulate_assembly(T: dict, sizes, stats, Lv: np.ndarray) -> np.ndarray:
-    """Replay prep, trsm and syrk kernels in FP64; returns the F buffer."""
+def tc_off(r: int, k: int, R: int) -> int:
+    """Byte offset of element (r, k) of an R x 32 digit block in the tcgen05
+    SYRK's shared-memory layout (canonical K-major, no swizzle)."""
+    return (k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2
+
+
+def check_tile_fetches(T: dict, t, yd_plane: int) -> None:
+    """The tcgen05 SYRK's 16-byte copies for one tile task: every source is
+    inside its supernode's digit block of one plane (16-byte aligned), every
+    destination inside the stage and the stage's A and B parts covered once."""
+    sns = T["sns"]
+    lst = T["syrk_list"][t["list_off"]:t["list_off"] + t["list_len"]]
+    j1lo, j2lo = int(t["q1"]) * 32, int(t["q2"]) * 32
+    j1min = max(j1lo, j2lo)
+    seen_a = set(tc_off(c, 8 * kc, 128) for c in range(128) for kc in range(4))
+    seen_b = set(tc_off(c, 8 * kc, 32) for c in range(32) for kc in range(4))
+    assert len(seen_a) == 512 and max(seen_a) + 16 <= 128 * 64 and all(o % 16 == 0 for o in seen_a)
+    assert len(seen_b) == 128 and max(seen_b) + 16 <= 32 * 64
+    for si in lst:
+        s = sns[si]
+        ns, ws = int(s["ns"]), int(s["jhi"] - s["jlo"])
+        npad = (ns + 31) // 32 * 32
+        for k0 in range(0, ns, 32):
+            if j1min >= T["cuts"][s["cut_off"] + k0 // 32]:
+                continue
+            for base, n in ((j1lo, 128), (j2lo, 32)):
+                for c in range(n):
+                    j = base + c - int(s["jlo"])
+                    if not (0 <= j < ws):
+                        continue
+                    for kc in range(4):
+                        e = int(s["yd_off"]) + j * npad + k0 + 8 * kc
+                        assert e % 8 == 0 and 0 <= e and e + 8 <= int(s["yd_off"]) + ws * npad <= yd_plane
+
+
+def emulate_assembly(T: dict, sizes, stats, Lv: np.ndarray, tile_subs=()) -> np.ndarray:
+    """Replay prep, trsm and syrk kernels in FP64; returns the F buffer.
+    Subdomains in tile_subs run the 128x32 tile SYRK (tcgen05 kernel)."""
     subs, sns, lcp, rmap = T["subs"], T["sns"], T["lcp"], T["rmap"]
     invd = np.zeros(int(T["header"]["n_cols"]))
     for g in T["active"]:
@@ -173,30 +212,35 @@ def emulate_assembly(T: dict, sizes, stats, Lv: np.ndarray) -> np.ndarray:
     for t in T["syrk"]:
         sd = subs[t["sub"]]
         lst = T["syrk_list"][t["list_off"]:t["list_off"] + t["list_len"]]
-        acc = np.zeros((32, 32))
+        tile = int(t["sub"]) in tile_subs
+        M = 128 if tile else 32
+        acc = np.zeros((M, 32))
         j1lo, j2lo = t["q1"] * 32, t["q2"] * 32
+        j1cut = max(j1lo, j2lo) if tile else j1lo   # the tile skips a block only if all its rows are cut
         for si in lst:
             s = sns[si]
             ws = s["jhi"] - s["jlo"]
             Ys = Y[s["y_off"]:s["y_off"] + s["ns"] * ws].reshape(s["ns"], ws).copy()
             for k0 in range(0, s["ns"], 32):          # blocks the kernel skips
-                if j1lo >= T["cuts"][s["cut_off"] + k0 // 32]:
+                if j1cut >= T["cuts"][s["cut_off"] + k0 // 32]:
                     Ys[k0:k0 + 32] = 0.0
-            A = np.zeros((s["ns"], 32))
+            A = np.zeros((s["ns"], M))
             B = np.zeros((s["ns"], 32))
-            for c in range(32):
-                ja, jb = j1lo + c - s["jlo"], j2lo + c - s["jlo"]
+            for c in range(M):
+                ja = j1lo + c - s["jlo"]
                 if 0 <= ja < ws:
                     A[:, c] = Ys[:, ja]
+            for c in range(32):
+                jb = j2lo + c - s["jlo"]
                 if 0 <= jb < ws:
                     B[:, c] = Ys[:, jb]
             assert not np.isnan(A).any() and not np.isnan(B).any(), "SYRK reads unwritten Y"
             acc += A.T @ B
         perm = T["perm"][sd["col_off"]:sd["col_off"] + sd["m"]]
-        for r in range(32):
+        for r in range(M):
             for c in range(32):
                 j1, j2 = j1lo + r, j2lo + c
-                if j1 < sd["m"] and j2 < sd["m"] and (t["q1"] != t["q2"] or j1 >= j2):
+                if j1 < sd["m"] and j2 < sd["m"] and (j1 >= j2 if tile else (t["q1"] != t["q2"] or j1 >= j2)):
                     a, b = perm[j1], perm[j2]
                     hi, lo = max(a, b), min(a, b)
                     I, J = hi // 32, lo // 32

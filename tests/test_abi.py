@@ -22,12 +22,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared(header):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(sc[A-Za-z_]*)\s*\(", src, flags=re.M))
+    return set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(sc\w*)\s*\(", src, flags=re.M))
 
 
 @pytest.mark.parametrize("header,loader", [("sc.h", _native.sc_lib), ("sc_dense.h", _native.dense_lib),
                                            ("sc_factor.h", _native.factor_lib), ("sc_implicit.h", _native.sc_lib),
-                                           ("sc_pipeline.h", _native.pipe_lib)])
+                                           ("sc_pipeline.h", _native.pipe_lib),
+                                           ("sc_probe.h", _native.sc_lib), ("sc_mlp.h", _native.sc_lib)])
 def test_library_exports_every_declared_symbol(header, loader):
     names = _declared(header)
     assert names, header
@@ -41,6 +42,7 @@ def test_binding_covers_header():
     assert _declared("sc_dense.h") == set(abi.DENSE_SYMBOLS)
     assert _declared("sc_implicit.h") == set(abi.IMPLICIT_SYMBOLS)
     assert _declared("sc_pipeline.h") == set(abi.PIPELINE_SYMBOLS)
+    assert _declared("sc_probe.h") == set(abi.PROBE_SYMBOLS)
 
 
 def _plan_raw(descs, n_dual):
@@ -165,6 +167,48 @@ def test_plan_emulation_matches_oracle(name, prob):
     Fo = oracle.dual_operators(prob.subdomains)
     for i in range(len(fs)):
         assert oracle.relative_frobenius(pe.export_dense(T, F, i), Fo[i]) <= 1e-12
+
+
+@pytest.mark.parametrize("name,prob", [c for c in _cases() if c[0] != "config1"] +
+                         [("mixed", synth.mixed_batch(lat2d=(2, 2), k2d=(6, 40), lat3d=(2, 1, 1), k3d=(2, 6), seed=3))],
+                         ids=lambda x: x if isinstance(x, str) else "")
+def test_tile_plan_emulation_matches_oracle(name, prob):
+    """Split-precision subdomains with the 128x32 tcgen05 SYRK tile (every
+    other subdomain, the rest 32x32 or FP64): the tile tasks' union lists,
+    their cut rule and their epilogue, replayed in FP64 on the CPU, give the
+    oracle's F with every entry written; every 16-byte copy the kernel issues
+    stays inside its supernode's digit block and the stage."""
+    fs = host.factorize_problem(prob.subdomains)
+    n = len(fs)
+    var = [(5, 7, 0)[i % 3] for i in range(n)]
+    tile = [i % 2 for i in range(n)]
+    plan = sc.Plan(fs, prob.n_dual, sub_slices=var, sub_tile=tile)
+    tile_subs = {i for i in range(n) if tile[i] and var[i]}
+    T = pe.export_plan(plan)
+    pe.check_bounds(T, plan.sizes, plan.stats, tile_subs)
+    lay = pe.check_split_layout(T, plan.sizes, plan.stats, sub_var=[v | (8 if i in tile_subs else 0)
+                                                                  for i, v in enumerate(var)])
+    for t in T["syrk"]:
+        if int(t["sub"]) in tile_subs:
+            pe.check_tile_fetches(T, t, lay["yd_plane"])
+    F = pe.emulate_assembly(T, plan.sizes, plan.stats, sc.concat_L_values(fs), tile_subs)
+    assert not np.isnan(F).any(), "F entries left unwritten"
+    Fo = oracle.dual_operators(prob.subdomains)
+    for i in range(n):
+        assert oracle.relative_frobenius(pe.export_dense(T, F, i), Fo[i]) <= 1e-12
+    ntile = sum(1 for t in T["syrk"] if int(t["sub"]) in tile_subs)
+    assert ntile > 0
+
+
+def test_tile_options_validated():
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    with pytest.raises(sc.SCError):
+        sc.Plan(fs, prob.n_dual, sub_slices=[5] * len(fs), sub_tile=[2] * len(fs))
+    with pytest.raises(sc.SCError):
+        sc.Plan(fs, prob.n_dual, tile=3)
+    with pytest.raises(sc.SCError):
+        sc.Plan(fs, prob.n_dual, poll_limit=-1)
 
 
 def _dense_factor_plan_stats(n, m):

@@ -71,3 +71,35 @@ def test_mixed_variants_in_one_batch(dev):
         assert err <= bound, (i, v, err)
         if v in (3, 4, 5):
             assert err > 1e-13                       # really ran in reduced precision
+
+
+@pytest.mark.parametrize("name", ["heat_cubes", "elasticity", "mixed"])
+def test_tcgen05_syrk_tile_matches_oracle_and_mma_sync(dev, name):
+    """The 128x32 SYRK tile on tcgen05 (sc_options.tile = SC_TILE_TC128): the
+    same digits and the same exact per-block group sums as the 32x32 mma.sync
+    blocks, so the two F agree to FP64 rounding (1e-15) and the tile meets the
+    digit count's bound against the oracle (7 digits: 1e-12)."""
+    if name == "heat_cubes":
+        prob = synth.cube_heat_3d(parts=2, k=9, coef_seed=5)
+    elif name == "elasticity":
+        prob = synth.elasticity_cubes((2, 2, 1), 3, 7, seed=4)
+    else:
+        prob = synth.mixed_batch(lat2d=(2, 2), k2d=(6, 40), lat3d=(2, 1, 1), k3d=(2, 6), seed=3)
+    fs = host.factorize_problem(prob.subdomains)
+    Fo = oracle.dual_operators(prob.subdomains, refine=1)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    for S in (7, 5):
+        out = {}
+        for tile in (abi.SC_TILE_32, abi.SC_TILE_TC128):
+            plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=S, tile=tile).upload(dev)
+            F = plan.new_F(dev)
+            F.fill_(float("nan"))
+            plan.assemble(Lv, F)
+            assert plan.device_status() == abi.SC_OK
+            assert bool(torch.isfinite(F).all())
+            out[tile] = [plan.export(F, i).cpu().numpy() for i in range(plan.nsub)]
+        for i in range(len(fs)):
+            diff = oracle.relative_frobenius(out[abi.SC_TILE_TC128][i], out[abi.SC_TILE_32][i])
+            err = oracle.relative_frobenius(out[abi.SC_TILE_TC128][i], Fo[i])
+            assert diff <= 1e-15, (S, i, diff)
+            assert err <= (1e-12 if S == 7 else 2.0 ** (-8 * S) * 1e3), (S, i, err)
