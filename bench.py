@@ -55,6 +55,19 @@ def _measured_hbm_gbps() -> float:
 HBM_PEAK_GBPS = _measured_hbm_gbps()
 
 
+def _measured_bf16_tflops() -> float:
+    """Dense BF16 tensor rate measured on this GPU model (cuBLAS burst,
+    MEASURED_PEAKS.json), else 1.9 PFLOP/s, an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
+BF16_PEAK_TFLOPS = _measured_bf16_tflops()
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -243,8 +256,45 @@ def _gpu_implicit(fs, n_dual, Lv, lam, q_expl, stream, reps=20):
     tf = ip.sizes.flops / (ms / 1e3) / 1e12
     diff = (torch.linalg.vector_norm(q - q_expl) / torch.linalg.vector_norm(q_expl)).item()
     return ms, {"ms": ms, "flops": ip.sizes.flops, "nnz_visited": int(ip.sizes.nnz_visited),
-                "max_levels": int(ip.sizes.max_levels), "tflops": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS,
+                "max_levels": int(ip.sizes.max_levels), "tflops": tf, "frac_fp64_peak_nominal": tf / FP64_PEAK_TFLOPS,
                 "rel_diff_vs_explicit": diff}
+
+
+def _fp64_fma_peak(dev, stream):
+    """The FP64 fused multiply-add rate of this GPU, measured (include/sc_probe.h):
+    8 independent chains per thread, 8 blocks of 256 threads per SM; CUDA
+    events on the launching stream, 3 warm-up launches, the best of 5."""
+    import ctypes
+
+    import torch
+
+    from paper_2509_21037_gb300 import _native
+    lib = _native.sc_lib()
+    flops, n = ctypes.c_double(), ctypes.c_int64()
+    iters, bps = 4096, 8
+    if lib.sc_probe_fp64_fma(iters, bps, None, ctypes.byref(flops), ctypes.byref(n), None) != 0:
+        raise RuntimeError("sc_probe_fp64_fma size query failed")
+    out = torch.empty(n.value, dtype=torch.float64, device=dev)
+    sp = _stream_ptr(stream)
+    for _ in range(3):
+        if lib.sc_probe_fp64_fma(iters, bps, out.data_ptr(), ctypes.byref(flops), ctypes.byref(n), sp) != 0:
+            raise RuntimeError("sc_probe_fp64_fma launch failed")
+    rates = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lib.sc_probe_fp64_fma(iters, bps, out.data_ptr(), ctypes.byref(flops), ctypes.byref(n), sp)
+        b.record(stream)
+        b.synchronize()
+        rates.append(flops.value / (a.elapsed_time(b) / 1e3) / 1e12)
+    if not bool(torch.isfinite(out).all()):
+        raise RuntimeError("FP64 probe produced non-finite values")
+    return max(rates), {"tflops_best": max(rates), "tflops_median": statistics.median(rates),
+                        "flops_per_launch": flops.value, "launches": 8}
+
+
+def _stream_ptr(stream):
+    return None if stream is None else int(stream.cuda_stream)
 
 
 def _secondary(section):
@@ -495,6 +545,16 @@ def run_sc(args):
     t_col = statistics.median(t_col)
     t_asm = sum(prep_ms) / len(prep_ms) + sum(trsm_ms) / len(trsm_ms) + sum(syrk_ms) / len(syrk_ms)
 
+    # the FP64 peak the roofline divides by: measured on this GPU, after the timed region
+    try:
+        fp64_peak, fp64_probe = _fp64_fma_peak(dev, stream)
+        peak_source = (f"measured: FP64 FMA probe (sc_probe_fp64_fma, best of 5 launches, CUDA events) "
+                       f"{fp64_peak:.3f} TFLOP/s (of measured); nominal 152 SMs x 4 flop/clk x 2.07 GHz "
+                       f"= {FP64_PEAK_TFLOPS:.3f}")
+    except Exception as e:  # report, fall back to the nominal figure
+        fp64_peak, fp64_probe = FP64_PEAK_TFLOPS, {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+        peak_source = "nominal: 152 SMs x 4 flop/clk x 2.07 GHz (the probe failed)"
+    gimpl["frac_fp64_peak"] = gimpl["tflops"] / fp64_peak
     # dominant kernel roofline (FP64 pipe)
     syrk_avg = sum(syrk_ms) / len(syrk_ms)
     trsm_avg = sum(trsm_ms) / len(trsm_ms)
@@ -511,10 +571,14 @@ def run_sc(args):
         "stage_ms": {"prep": sum(prep_ms) / len(prep_ms), "trsm": trsm_avg, "syrk": syrk_avg},
         "flops": {"useful_trsm": st["flops_trsm"], "useful_syrk": st["flops_syrk"],
                   "dense_equivalent": st["flops_dense"]},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": _traffic_for(dom),
-                     "peak_source": "FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe FP64 1.25 TFLOP/s)"},
+                     "peak_source": peak_source, "peak_nominal": FP64_PEAK_TFLOPS,
+                     "frac_of_nominal": achieved / FP64_PEAK_TFLOPS, "fp64_probe": fp64_probe,
+                     "other_kernel": {"kernel": "trsm_kernel" if dom == "syrk_kernel" else "syrk_kernel",
+                                      "frac": (st["flops_trsm"] / (trsm_avg / 1e3) / 1e12 if dom == "syrk_kernel"
+                                               else st["flops_syrk"] / (syrk_avg / 1e3) / 1e12) / fp64_peak}},
         "e2e": {"value": world * nsub / (e2e_serial_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(Lpin.numel() * 8 + lam_pin.numel() * 8),
                 "d2h_bytes_per_step": int(q_pin.numel() * 8),
@@ -591,8 +655,8 @@ def _split_section(args, fs, prob, Lv, lam, flush, stream, dev, fp64_ms):
     from paper_2509_21037_gb300 import abi, sc
     Fo = oracle.dual_operators(prob.subdomains, refine=1) if args.split_error else None
     out = {}
-    for S in args.split_slices:
-        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=S).upload(dev)
+    for S, tile in [(S, t) for S in args.split_slices for t in (abi.SC_TILE_32, abi.SC_TILE_TC128)]:
+        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=S, tile=tile).upload(dev)
         F = plan.new_F(dev)
         q = torch.empty_like(lam)
         for _ in range(args.warmup):
@@ -621,10 +685,20 @@ def _split_section(args, fs, prob, Lv, lam, flush, stream, dev, fp64_ms):
                "stage_ms": {"trsm": sum(trsm) / len(trsm), "syrk": sum(syrk) / len(syrk)},
                "tensor_products_per_fp64_product": S * (S + 1) // 2,
                "useful_fp64_equivalent_tflops": (st["flops_trsm"] + st["flops_syrk"]) / (ms / 1e3) / 1e12}
+        # tensor roofline: useful FP64 flops x digit products per FP64 product = the BF16 work done
+        P = S * (S + 1) // 2
+        syrk_stage = rec["stage_ms"]["syrk"]
+        step_tf = (st["flops_trsm"] + st["flops_syrk"]) * P / (ms / 1e3) / 1e12
+        syrk_tf = st["flops_syrk"] * P / (syrk_stage / 1e3) / 1e12
+        rec["roofline"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": BF16_PEAK_TFLOPS,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst, of measured)",
+                           "step": {"achieved": step_tf, "frac": step_tf / BF16_PEAK_TFLOPS},
+                           "syrk_stage": {"achieved": syrk_tf, "frac": syrk_tf / BF16_PEAK_TFLOPS}}
         if Fo is not None:
             errs = [oracle.relative_frobenius(plan.export(F, i).cpu().numpy(), Fo[i]) for i in range(len(fs))]
             rec["rel_frobenius_error"] = {"max": max(errs), "median": float(np.median(errs)), "min": min(errs)}
-        out[f"slices_{S}"] = rec
+        rec["syrk_tile"] = "128x32 tcgen05.mma (TMEM accumulators)" if tile else "32x32 mma.sync"
+        out[f"slices_{S}" + ("_tc128" if tile else "")] = rec
         del plan, F
     return out
 
