@@ -1,10 +1,12 @@
 """Per-subdomain kernel-variant selection: measuring autotuner and learned predictor.
 
-The assembly offers, per subdomain, FP64 or split precision with 4..7 digits
-(include/sc.h, sc_options.sub_slices).  Which one is fastest depends on the
-subdomain (small or narrow subdomains do not repay the digit-plane overhead;
-large ones gain up to ~3x), and which ones are accurate enough depends on the
-error target.  This module
+The assembly offers, per subdomain, FP64 or split precision with 3..7 digits
+(include/sc.h, sc_options.sub_slices) and, for split precision, two SYRK
+output tiles: 32x32 blocks on the warp-level tensor-core instruction or
+128x32 tiles on tcgen05 (sc_options.sub_tile).  Which one is fastest depends
+on the subdomain (small or narrow subdomains do not repay the digit-plane
+overhead or fill the large tile; large ones gain up to ~3x), and which ones
+are accurate enough depends on the error target.  This module
 
   * describes every subdomain by sparsity-pattern features from its plan
     (sizes, supernode structure, flop counts) and one value feature (the
@@ -15,7 +17,9 @@ error target.  This module
   * ``LearnedSelector``: trains the GPU MLP (include/sc_mlp.h) on those
     records to predict log time and log error of every variant from the
     features, and picks per subdomain the fastest variant predicted to meet
-    the error target.  Classes the autotuner has measured keep its measured
+    the error target -- through the C ABI (sc_select: the library computes the
+    features from the plan, runs the forward pass and applies the rule).
+    Classes the autotuner has measured keep its measured
     choice (the fallback); on the others the measured choice, when available,
     is the yardstick of the learned choice's regret.
 """
@@ -29,7 +33,25 @@ import numpy as np
 
 from . import abi, sc
 
-VARIANTS: Tuple[int, ...] = (0, 7, 6, 5, 4)        # 0 = FP64, k = split with k digits
+# A variant is coded as digits + 8 * tile: 0 = FP64; S = split with S digits and
+# 32x32 SYRK blocks (mma.sync); 8 + S = S digits with the 128x32 SYRK tile on
+# tcgen05 (include/sc.h: sub_slices, sub_tile).  The structural choice (tile)
+# and the arithmetic one (digits) are chosen jointly.
+TILE = 8
+VARIANTS: Tuple[int, ...] = (0, 7, 7 + TILE, 5, 5 + TILE)
+
+
+def digits(v: int) -> int:
+    return int(v) & 7
+
+
+def tile(v: int) -> int:
+    return int(v) >> 3
+
+
+def plan_options(var: Sequence[int]) -> dict:
+    """sc.Plan keyword arguments for per-subdomain variant codes."""
+    return {"sub_slices": [digits(v) for v in var], "sub_tile": [tile(v) for v in var]}
 FEATURES = ("log2_n", "log2_m", "log2_nnzL", "log2_supernodes", "log2_max_supernode", "log2_flops_trsm",
             "log2_flops_syrk", "log2_flops_dense", "log2_y_doubles", "log2_diag_spread")
 
@@ -45,23 +67,19 @@ def class_key(f) -> tuple:
     return (f.n, f.L.nnz, int(round(4 * math.log2(max(f.m, 1)))), hash(f.L.rowind.tobytes()))
 
 
-def subdomain_features(fs: Sequence) -> np.ndarray:
-    """[nsub, len(FEATURES)]; one single-subdomain plan per structural class."""
-    cache: Dict[tuple, np.ndarray] = {}
-    out = np.zeros((len(fs), len(FEATURES)))
-    for i, f in enumerate(fs):
-        k = class_key(f)
-        if k not in cache:
-            p = sc.Plan([f], int(np.max(f.lambda_map)) + 1 if f.m else 1)
-            st = p.stats
-            cache[k] = np.array([_log2(f.n), _log2(f.m), _log2(f.L.nnz), _log2(st.n_supernodes),
-                                 _log2(st.max_supernode), _log2(st.flops_trsm), _log2(st.flops_syrk),
-                                 _log2(st.flops_dense), _log2(st.y_doubles), 0.0])
-        v = cache[k].copy()
-        d = f.L.values[f.L.colptr[:-1]]
-        v[-1] = math.log2(float(d.max() / d.min()))
-        out[i] = v
-    return out
+def subdomain_features(fs: Sequence, plan=None) -> np.ndarray:
+    """[nsub, len(FEATURES)], computed by the library from the batch plan
+    (include/sc.h, sc_subdomain_features), the same features sc_select uses."""
+    import ctypes
+    if plan is None:
+        plan = sc.Plan(fs, max((int(np.max(f.lambda_map)) + 1 for f in fs if f.m), default=1))
+    out = np.zeros((len(fs), abi.SC_NUM_FEATURES), np.float32)
+    vals = sc.concat_L_values(fs)
+    rc = plan.lib.sc_subdomain_features(plan.h, vals.ctypes.data if vals.size else None,
+                                        out.ctypes.data if out.size else None)
+    if rc != 0:
+        raise sc.SCError(rc, plan.lib.sc_last_error(plan.h).decode())
+    return out.astype(np.float64)
 
 
 @dataclasses.dataclass
@@ -75,7 +93,7 @@ class ClassRecord:
 
 def _time_variant(batch, n_dual, v, device, reps):
     import torch
-    plan = sc.Plan(batch, n_dual, sub_slices=[v] * len(batch)).upload(device)
+    plan = sc.Plan(batch, n_dual, **plan_options([v] * len(batch))).upload(device)
     Lv = torch.from_numpy(sc.concat_L_values(batch)).to(device)
     F = plan.new_F(device)
     plan.assemble(Lv, F)
@@ -114,7 +132,8 @@ def measure_class(f, device, variants=VARIANTS, reps: int = 3, target_flops: flo
 
 def autotune(fs: Sequence, device, variants=VARIANTS, classes: Optional[Sequence[tuple]] = None,
              reps: int = 3) -> Dict[tuple, ClassRecord]:
-    """Measure every (or the listed) structural class of the batch."""
+    """Measure every (or the listed) structural class of the batch, over the
+    joint (digits, SYRK tile) variant space."""
     feats = subdomain_features(fs)
     groups: Dict[tuple, List[int]] = {}
     for i, f in enumerate(fs):
@@ -170,24 +189,53 @@ class LearnedSelector:
         return times, errs
 
     def choose(self, X: np.ndarray, tol: float, margin: float = 10.0) -> List[int]:
+        """Variant codes for feature rows X (the rule of sc_select, evaluated here)."""
         times, errs = self.predict(X)
         return [best_variant(t, e, tol, margin) for t, e in zip(times, errs)]
+
+    def c_selector(self):
+        """The trained network as an include/sc.h sc_selector (kept alive on self)."""
+        import ctypes
+        self._sel_arrays = [np.ascontiguousarray(a) for a in (
+            np.array([digits(v) for v in self.variants], np.int8), np.array([tile(v) for v in self.variants], np.int8),
+            self.net.mu.astype(np.float32), self.net.sd.astype(np.float32),
+            self.tmu.astype(np.float32), self.tsd.astype(np.float32))]
+        sl, tl, xm, xs, ym, ys = self._sel_arrays
+        return abi.Selector(len(self.variants), sl.ctypes.data, tl.ctypes.data, self.net.dims[1],
+                            self.net.params.data_ptr(), xm.ctypes.data, xs.ctypes.data, ym.ctypes.data, ys.ctypes.data)
+
+    def select_batch(self, fs: Sequence, tol: float, margin: float = 10.0, plan=None) -> List[int]:
+        """Per-subdomain variant codes through the C ABI (sc_select): the
+        library computes the features from the plan, runs the network's
+        forward pass on the GPU and applies the choice rule."""
+        import ctypes
+
+        import torch
+        if plan is None:
+            plan = sc.Plan(fs, max((int(np.max(f.lambda_map)) + 1 for f in fs if f.m), default=1))
+        sel = self.c_selector()
+        need = ctypes.c_size_t()
+        plan._check(plan.lib.sc_select_workspace(plan.h, ctypes.byref(sel), ctypes.byref(need)))
+        ws = torch.empty(max(1, need.value), dtype=torch.float32, device=self.net.device)
+        vals = sc.concat_L_values(fs)
+        sl = np.zeros(len(fs), np.int8)
+        tl = np.zeros(len(fs), np.int8)
+        plan._check(plan.lib.sc_select(plan.h, ctypes.byref(sel), vals.ctypes.data if vals.size else None,
+                                       float(tol), float(margin), ws.data_ptr(), ws.numel(),
+                                       sl.ctypes.data, tl.ctypes.data, None))
+        return [int(s) + TILE * int(t) for s, t in zip(sl, tl)]
 
 
 def select(fs: Sequence, tol: float, selector: Optional[LearnedSelector] = None,
            measured: Optional[Dict[tuple, ClassRecord]] = None, margin: float = 10.0) -> List[int]:
-    """Per-subdomain variants: measured classes use the autotuner's choice,
-    the others the learned prediction (FP64 when neither is available)."""
+    """Per-subdomain variant codes: measured classes use the autotuner's
+    choice, the others the learned prediction through sc_select (FP64 when
+    neither is available)."""
     out = [0] * len(fs)
-    need = []
+    if selector is not None:
+        out = selector.select_batch(fs, tol, margin)
     for i, f in enumerate(fs):
         rec = measured.get(class_key(f)) if measured else None
         if rec is not None:
             out[i] = best_variant(rec.time_ms, rec.error, tol)
-        else:
-            need.append(i)
-    if need and selector is not None:
-        X = subdomain_features([fs[i] for i in need])
-        for i, v in zip(need, selector.choose(X, tol, margin)):
-            out[i] = v
     return out
