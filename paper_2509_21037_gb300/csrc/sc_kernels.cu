@@ -444,7 +444,7 @@ int launch_group_syrk(const sc_ctx &c, int w, int v, const double *Y, void *ws, 
     return (int)cudaGetLastError();
   }
   const int S = var_digits(v);
-  int e = launch_yslice_group(c, S, G.sblk[v][0], G.sblk[v][1], Y, ws, stream);
+  int e = launch_yslice_group(c, S, G.sblk[v][0], G.sblk[v][1], Y, ws, stream, (v & kVarTile) != 0);
   if (e) return e;
   if (v & kVarTile) return launch_syrk_tc(c, S, G.syrk[v][0], G.syrk[v][1], ws, F, stream);
   return launch_syrk_split(c, S, G.syrk[v][0], G.syrk[v][1], ws, F, stream);

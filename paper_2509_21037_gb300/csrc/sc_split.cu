@@ -129,7 +129,12 @@ __global__ void __launch_bounds__(kThreads) ycolexp_kernel(const PlanPtrs P, con
 // Digit planes of Y for one (supernode, 32-row block) item: 32x32 tiles are
 // read row-wise (coalesced), transposed in shared memory and written
 // column-major (coalesced), rows padded to 32.
-template <int S>
+// kBalanced (the tcgen05 SYRK's planes): the magnitude is cut against twice the
+// column bound (|y| 2^-(Ej + 1) < 1/2, so the top digit is at most 127) and
+// recoded into balanced digits in [-128, 128] (least significant first: a
+// digit above 127 becomes digit - 256 and carries one into the next), so
+// every digit product is at most 2^14 in magnitude.
+template <int S, bool kBalanced>
 __global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, const double *__restrict__ Y,
                                                           const int *__restrict__ colexp,
                                                           __nv_bfloat16 *__restrict__ Yd, int64_t yd_plane) {
@@ -151,10 +156,25 @@ __global__ void __launch_bounds__(kThreads) yslice_kernel(const PlanPtrs P, cons
       const int c = c0 + j;
       if (c < ws) {
         const double v = Ts[lane][j];
-        const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c]);
         const int64_t e = s.yd_off + (int64_t)c * npad + r0 + lane;
+        if (kBalanced) {
+          const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c] + 1);
+          int dig[S];
+          int carry = 0;
 #pragma unroll
-        for (int d = 0; d < S; ++d) Yd[(int64_t)d * yd_plane + e] = digit_bf16(X, d, v < 0.0);
+          for (int d = S - 1; d >= 0; --d) {
+            int u = (int)((X >> (55 - 8 * d)) & 0xFF) + carry;
+            carry = (d > 0 && u >= 128) ? 1 : 0;
+            dig[d] = u - 256 * carry;
+          }
+#pragma unroll
+          for (int d = 0; d < S; ++d)
+            Yd[(int64_t)d * yd_plane + e] = __float2bfloat16_rn(v < 0.0 ? -(float)dig[d] : (float)dig[d]);
+        } else {
+          const uint64_t X = fixed_point(v, colexp[sd.col_off + s.jlo + c]);
+#pragma unroll
+          for (int d = 0; d < S; ++d) Yd[(int64_t)d * yd_plane + e] = digit_bf16(X, d, v < 0.0);
+        }
       }
     }
     __syncthreads();
@@ -350,6 +370,29 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
       const int kw = min(32, s.ns - kb);
       const int wk = min(b, P.cuts[s.cut_off + (kb >> 5)]) - a;
       if (wk <= 0) continue;
+      const int nb = nrow - (kb + kw);
+      const int64_t base = s.ld_off + (int64_t)blk * nrow - 16LL * blk * (blk + 1);
+      // the L digit fragments of a warp's first m-tile depend on L only: the
+      // warps that do not solve the triangle fetch them while it is solved
+      uint32_t afr[S][2][4];
+      auto load_afr = [&](int mt) {
+        const int ra = mt * 16 + g, rb = ra + 8;
+        const bool va = ra < nb, vb = rb < nb;
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+          const uint32_t *pa = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + ra) * 32);
+          const uint32_t *pb = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + rb) * 32);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            afr[d][ks][0] = va ? pa[8 * ks + tg] : 0u;
+            afr[d][ks][1] = vb ? pb[8 * ks + tg] : 0u;
+            afr[d][ks][2] = va ? pa[8 * ks + tg + 4] : 0u;
+            afr[d][ks][3] = vb ? pb[8 * ks + tg + 4] : 0u;
+          }
+        }
+      };
+      const bool pre = warp != tri && warp * 16 < nb;
+      if (pre) load_afr(warp);
       if (warp == tri) {
         if (lane < kw) cps[lane] = cp[kb + lane] - (kb + lane);
         __syncwarp();
@@ -370,7 +413,6 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
         emaxX[lane] = em;
       }
       __syncthreads();
-      const int nb = nrow - (kb + kw);
       if (nb <= 0) continue;                  // nothing below this block (uniform)
       for (int e = tid; e < 32 * 32; e += kThreads) {
         const int q = e >> 5, c = e & 31;
@@ -381,25 +423,12 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
         for (int d = 0; d < S; ++d) PX[d][c][q] = digit_bf16(X, d, neg);
       }
       __syncthreads();
-      const int64_t base = s.ld_off + (int64_t)blk * nrow - 16LL * blk * (blk + 1);
       for (int mt = warp; mt * 16 < nb; mt += kThreads / 32) {
         const int r0 = mt * 16;               // first block row of this m-tile
         const int ra = r0 + g, rb = r0 + g + 8;
         const bool va = ra < nb, vb = rb < nb;
         const int ea = va ? lexp[base + ra] : 0, eb = vb ? lexp[base + rb] : 0;
-        uint32_t afr[S][2][4];
-#pragma unroll
-        for (int d = 0; d < S; ++d) {
-          const uint32_t *pa = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + ra) * 32);
-          const uint32_t *pb = reinterpret_cast<const uint32_t *>(Ld + (int64_t)d * ld_rows * 32 + (base + rb) * 32);
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            afr[d][ks][0] = va ? pa[8 * ks + tg] : 0u;
-            afr[d][ks][1] = vb ? pb[8 * ks + tg] : 0u;
-            afr[d][ks][2] = va ? pa[8 * ks + tg + 4] : 0u;
-            afr[d][ks][3] = vb ? pb[8 * ks + tg + 4] : 0u;
-          }
-        }
+        if (!(pre && mt == warp)) load_afr(mt);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
           if (8 * nt >= wk) break;                   // uniform across the warp
@@ -493,7 +522,7 @@ int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream) {
 }
 
 int launch_yslice_group(const sc_ctx &c, int S_, int64_t base, int64_t count, const double *Y, void *ws,
-                        void *stream) {
+                        void *stream, bool balanced) {
   if (count <= 0) return (int)cudaGetLastError();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t *w = static_cast<uint8_t *>(ws);
@@ -502,9 +531,15 @@ int launch_yslice_group(const sc_ctx &c, int S_, int64_t base, int64_t count, co
   PlanPtrs p = c.ptrs();
   p.sblk += 2 * base;
   ycolexp_kernel<<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp);
-#define YS(S) yslice_kernel<S><<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
-  SC_SPLIT_SWITCH(S_, YS)
+#define YS(S) yslice_kernel<S, false><<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
+#define YB(S) yslice_kernel<S, true><<<(unsigned)count, kThreads, 0, st>>>(p, Y, colexp, Yd, c.ws.yd_plane)
+  if (balanced) {
+    SC_SPLIT_SWITCH(S_, YB)
+  } else {
+    SC_SPLIT_SWITCH(S_, YS)
+  }
 #undef YS
+#undef YB
   return (int)cudaGetLastError();
 }
 

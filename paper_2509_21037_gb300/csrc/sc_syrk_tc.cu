@@ -14,7 +14,7 @@
 //     the FP64 values of Y against per-column exponent bounds) are copied
 //     into shared memory in the canonical K-major layout without swizzle
 //     (8-row x 16-byte core matrices) by 16-byte asynchronous copies, three
-//     stages deep;
+//     stages deep, two blocks ahead of the tensor cores;
 //   * one thread issues, for every digit group d = t + t' < S and every pair
 //     (t, t'), two tcgen05.mma kind::f16 (M = 128, N = 32, K = 16; BF16 in,
 //     FP32 accumulate) into the group's 32 accumulator columns in tensor
@@ -22,8 +22,13 @@
 //   * while the tensor cores run the next block into the other of two
 //     accumulator buffers, the eight warps read the finished buffer back
 //     (tcgen05.ld; warp w owns tensor-memory lanes 32 (w mod 4) .. and
-//     columns 16 (w / 4) ..), and fold the exact group sums (integers below
-//     7 * 32 * 255^2 < 2^24, exact in FP32) into 64-bit integer Horner words.
+//     columns 16 (w / 4) ..) and add the exact group sums into 32-bit
+//     integers with one FP32 add and one integer add each: the planes hold
+//     balanced digits (|digit| <= 128, yslice_kernel), so a group's block sum
+//     is an integer below 7 * 32 * 2^14 < 2^22, where FP32 is exact and
+//     v + 1.5 * 2^23 puts v in the low mantissa bits; every 256 blocks and at
+//     the end the groups are combined exactly in 64-bit integers (Horner) and
+//     added to one FP64 value per output.
 // The epilogue forms each output with one conversion to FP64 and one scaling
 // and writes it in the user's column order, as the mma.sync kernel does.
 //
@@ -145,7 +150,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   };
   // 16-byte copies of one block's digit planes into stage `st`: per plane,
-  // 128 + 32 columns x 4 chunks of 8 rows; columns outside [jlo, jhi) are zero
+  // 128 + 32 columns x 4 chunks of 8 rows; columns outside [jlo, jhi) are zero.
+  // Eight consecutive threads take eight consecutive columns of one chunk, so
+  // the eight 16-byte stores of a shared-memory wavefront land in distinct
+  // banks (their offsets differ in (column mod 8) * 16); the four chunks of a
+  // column (64 contiguous bytes of Y's digits) come from the same warp.
   auto fetch = [&](int li, int k0, int st) {
     const SnDev sn = P.sns[P.syrk_list[t.list_off + li]];
     const int npad = (sn.ns + 31) / 32 * 32;
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr int kPer = (kTileM + kTileN) * 4;      // copies per plane
     for (int v = tid; v < S * kPer; v += kTcThreads) {
       const int d = v / kPer, w = v - d * kPer;
-      const int col = w >> 2, kc = w & 3;
+      const int kc = (w >> 3) & 3, col = (w & 7) | ((w >> 5) << 3);
       const bool isA = col < kTileM;
       const int c = isA ? col : col - kTileM;
       const int j = (isA ? j1lo : j2lo) + c - sn.jlo;
@@ -170,11 +179,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // per thread: tensor-memory lane quarter and its 16 of the tile's 32 columns
   const int quarter = warp & 3, chalf = warp >> 2;
   const int row = 32 * quarter + lane;                        // tile row (j1 - j1lo)
-  Groups<S> acc[16];
+  // Block sums of digit group d are integers of magnitude below 7 * 32 * 2^14 <
+  // 2^22 (balanced digits), so v + 1.5 * 2^23 is exact and its bit pattern is
+  // 0x4B400000 + v: one FP32 add and one 32-bit integer add per value fold a
+  // block into gs (wrapping; the 0x4B400000 per block is taken out at the fold,
+  // exact while the true sum stays below 2^31: at most 256 blocks).
+  uint32_t gs[S][16];
   double dacc[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) dacc[c] = 0.0;
-  int folded = 0;
+  for (int c = 0; c < 16; ++c) {
+    dacc[c] = 0.0;
+#pragma unroll
+    for (int d = 0; d < S; ++d) gs[d][c] = 0u;
+  }
+  uint32_t nfold = 0;
+  auto fold = [&]() {                      // exact: int64 Horner words, then one FP64 value per output
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      Groups<S> g;
+#pragma unroll
+      for (int d = 0; d < S; ++d) {
+        g.accumulate(d, (int)(gs[d][c] - nfold * 0x4B400000u));
+        gs[d][c] = 0u;
+      }
+      dacc[c] += g.value_wide();
+    }
+    nfold = 0;
+  };
 
   auto flush = [&](int nb) -> bool {       // fold block nb's accumulators (buffer nb & 1)
     if (!mbar_wait(smem_u32(&mbar[nb & 1]), (uint32_t)((nb >> 1) & 1), poll_limit)) return false;
@@ -190,34 +221,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           : "r"(tb + 32u * d));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc[c].accumulate(d, __float2int_rn(__uint_as_float(v[c])));
+      for (int c = 0; c < 16; ++c) gs[d][c] += __float_as_uint(__uint_as_float(v[c]) + 12582912.0f);
     }
-    if (++folded == 128) {                 // int64 headroom (as in the mma.sync kernel)
-      folded = 0;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        dacc[c] += acc[c].value_wide();
-        acc[c] = Groups<S>();
-      }
-    }
+    if (++nfold == 256) fold();
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     return true;
   };
 
-  int li = 0, k0 = -32, nb = 0;
-  bool have = advance(li, k0);
-  if (have) fetch(li, k0, 0);
+  // Three stages, two blocks in flight ahead of the tensor cores: in iteration
+  // nb the MMAs of block nb are issued, block nb - 1 is folded (its MMAs are
+  // then complete, so its stage is free) and block nb + 2 is fetched into
+  // that stage while block nb + 1's copies finish.  Every iteration commits
+  // exactly one copy group (possibly empty), so `wait_group 1` always means
+  // "all but the newest group", i.e. block nb + 1.
+  int li0 = 0, k00 = -32;
+  bool have = advance(li0, k00);
+  int li1 = li0, k01 = k00;
+  bool h1 = have && advance(li1, k01);
+  int li2 = li1, k02 = k01;
+  bool h2 = h1 && advance(li2, k02);
+  if (have) fetch(li0, k00, 0);
+  else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  if (h1) fetch(li1, k01, 1);
+  else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // the copies, seen by the tensor cores
+  __syncthreads();
+  int nb = 0;
   while (have) {
-    int nli = li, nk0 = k0;
-    const bool nhave = advance(nli, nk0);
-    if (nhave) {
-      fetch(nli, nk0, (nb + 1) % kStages);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // the copies, seen by the tensor cores
-    __syncthreads();
     if (abort_flag) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n");
@@ -243,9 +274,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       atomicOr(status, kStatusTimeout);
       abort_flag = 1;
     }
-    li = nli;
-    k0 = nk0;
-    have = nhave;
+    // stage (nb + 2) % 3 held block nb - 1, whose MMAs this thread has seen complete
+    if (h2) fetch(li2, k02, (nb + 2) % kStages);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    have = h1;
+    h1 = h2;
+    li1 = li2;
+    k01 = k02;
+    if (h2) h2 = advance(li2, k02);
     ++nb;
   }
   __syncthreads();
@@ -257,7 +297,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
   if (!ok || abort_flag) return;
 
-  // epilogue: row j1 of the tile, columns j2 = j2lo + 16 chalf + c
+  fold();
+  // epilogue: row j1 of the tile, columns j2 = j2lo + 16 chalf + c; the balanced
+  // digits were cut against twice each column bound: 2^(Ej + 1) per operand
   const int32_t *perm = P.perm_cols + sd.col_off;
   const int *ce = colexp + sd.col_off;
   const int j1 = j1lo + row;
@@ -266,8 +308,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int c = 0; c < 16; ++c) {
       const int j2 = j2lo + 16 * chalf + c;
       if (j2 >= sd.m || j1 < j2) continue;
-      double v = dacc[c] + acc[c].value_wide();
-      const int e = (ce[j1] - 1022) + (ce[j2] - 1022);
+      double v = dacc[c];
+      const int e = (ce[j1] + 1 - 1022) + (ce[j2] + 1 - 1022);
       v = (e >= -1022 && e <= 1023) ? v * pow2i(e) : ldexp(v, e);
       const int a = perm[j1], b = perm[j2];
       const int hi = max(a, b), lo = min(a, b);

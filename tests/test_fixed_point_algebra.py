@@ -77,3 +77,39 @@ def test_fixed_point_zero_block_and_tile():
     lam = np.ones(32)
     assert np.all(_tile_rows(T, lam) == 0.0)
     assert np.all(_tile_rows(np.ones((32, 32)), np.zeros(32)) == 0.0)
+
+
+def _balanced_digits(X, S):
+    """The recoding of the tcgen05 SYRK's Y planes (yslice_kernel, balanced):
+    the S top bytes of a 62-bit magnitude, least significant first, a digit
+    above 127 becomes digit - 256 and carries one into the next; the top
+    digit takes the last carry without wrapping."""
+    dig = [0] * S
+    carry = 0
+    for d in range(S - 1, -1, -1):
+        u = ((X >> (55 - 8 * d)) & 0xFF) + carry
+        carry = 1 if (d > 0 and u >= 128) else 0
+        dig[d] = u - 256 * carry
+    return dig
+
+
+def test_balanced_digits_reconstruct_and_stay_small():
+    """Balanced digits of a magnitude below 2^62 lie in [-128, 128] (so every
+    digit product is at most 2^14 and a 32-row block sum of up to 7 digit
+    pairs stays below 7 * 32 * 2^14 < 2^22, the range where the kernel's
+    FP32-to-integer step v + 1.5 * 2^23 is exact) and represent exactly the
+    magnitude truncated to its top S bytes."""
+    rng = np.random.default_rng(11)
+    cases = [0, 1, (1 << 62) - 1, (1 << 61), 0x7F7F7F7F7F7F7F7F >> 1] + \
+        [int(x) for x in rng.integers(0, 1 << 62, size=4000, dtype=np.uint64)]
+    for S in (3, 4, 5, 6, 7):
+        for X in cases:
+            X &= (1 << 62) - 1
+            dig = _balanced_digits(X, S)
+            assert all(-128 <= d <= 128 for d in dig)
+            assert sum(d * 256 ** (S - 1 - t) for t, d in enumerate(dig)) == X >> (55 - 8 * (S - 1))
+    assert 7 * 32 * 128 * 128 < 2 ** 22
+    # v + 1.5 * 2^23 in FP32 puts v in the low bits for |v| < 2^22
+    for v in (0, 1, -1, 3670016, -3670016, 2 ** 22 - 1, -(2 ** 22 - 1)):
+        bits = struct.unpack("<I", struct.pack("<f", np.float32(v) + np.float32(12582912.0)))[0]
+        assert bits - 0x4B400000 == v

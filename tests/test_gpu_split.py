@@ -75,10 +75,11 @@ def test_mixed_variants_in_one_batch(dev):
 
 @pytest.mark.parametrize("name", ["heat_cubes", "elasticity", "mixed"])
 def test_tcgen05_syrk_tile_matches_oracle_and_mma_sync(dev, name):
-    """The 128x32 SYRK tile on tcgen05 (sc_options.tile = SC_TILE_TC128): the
-    same digits and the same exact per-block group sums as the 32x32 mma.sync
-    blocks, so the two F agree to FP64 rounding (1e-15) and the tile meets the
-    digit count's bound against the oracle (7 digits: 1e-12)."""
+    """The 128x32 SYRK tile on tcgen05 (sc_options.tile = SC_TILE_TC128): its
+    balanced digits (against twice each column bound) truncate at a different
+    place than the 32x32 mma.sync path's unsigned digits, so the two F agree
+    to the digit truncation (2^-8S times the growth factor 1e3), and the tile
+    meets the digit count's bound against the oracle (7 digits: 1e-12)."""
     if name == "heat_cubes":
         prob = synth.cube_heat_3d(parts=2, k=9, coef_seed=5)
     elif name == "elasticity":
@@ -101,5 +102,5 @@ def test_tcgen05_syrk_tile_matches_oracle_and_mma_sync(dev, name):
         for i in range(len(fs)):
             diff = oracle.relative_frobenius(out[abi.SC_TILE_TC128][i], out[abi.SC_TILE_32][i])
             err = oracle.relative_frobenius(out[abi.SC_TILE_TC128][i], Fo[i])
-            assert diff <= 1e-15, (S, i, diff)
+            assert diff <= 2.0 ** (-8 * S) * 1e3, (S, i, diff)
             assert err <= (1e-12 if S == 7 else 2.0 ** (-8 * S) * 1e3), (S, i, err)

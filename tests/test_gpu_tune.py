@@ -1,8 +1,10 @@
 """Autotuner and learned variant selector on a mixed 2D heat / 3D elasticity
-batch: the MLP, trained on the autotuner's records of half of the subdomain
-classes, picks variants for the other half; the autotuner's own measurements
-there measure its regret; the selected batch must beat the FP64-only batch and
-meet the error target."""
+batch, over the joint variant space (digits x SYRK tile: FP64, 7 or 5 digits
+with 32x32 mma.sync blocks or 128x32 tcgen05 tiles): the MLP, trained on the
+autotuner's records of half of the subdomain classes, picks variants for the
+other half; the autotuner's own measurements there measure its regret; the
+batch selection runs through the C ABI (sc_select) and must beat the
+FP64-only batch and every uniform choice, and meet the error target."""
 import numpy as np
 import pytest
 
@@ -21,7 +23,7 @@ def dev():
 
 
 def _batch_ms(fs, n_dual, dev, var, reps=3):
-    plan = sc.Plan(fs, n_dual, sub_slices=var).upload(dev)
+    plan = sc.Plan(fs, n_dual, **tune.plan_options(var)).upload(dev)
     Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
     F = plan.new_F(dev)
     plan.assemble(Lv, F)
@@ -38,7 +40,7 @@ def _batch_ms(fs, n_dual, dev, var, reps=3):
 def test_learned_selector_gain_and_regret(dev):
     prob = synth.mixed_batch(lat2d=(6, 6), k2d=(12, 48), lat3d=(4, 3, 2), k3d=(3, 9), seed=3)
     fs = host.factorize_problem(prob.subdomains)
-    V = (0, 7, 5, 4)
+    V = tune.VARIANTS
     recs = tune.autotune(fs, dev, variants=V, reps=2)
     for k in sorted(recs, key=lambda k: recs[k].features[0]):
         r = recs[k]
@@ -59,13 +61,17 @@ def test_learned_selector_gain_and_regret(dev):
           f"feasible {np.mean(feasible):.2f}")
     assert all(feasible)
     assert np.mean(regrets) < 0.25
+    # the batch choice through the C ABI: held-out classes from sc_select, measured ones from the autotuner
     var = tune.select(fs, tol, sel, measured={k: recs[k] for k in train})
+    assert set(var) <= set(V)
+    for i, f in enumerate(fs):
+        r = recs.get(tune.class_key(f))
+        if r is not None and var[i]:
+            assert r.error[var[i]] <= tol, (i, var[i], r.error[var[i]])
     t_sel = _batch_ms(fs, prob.n_dual, dev, var)
-    t_fp64 = _batch_ms(fs, prob.n_dual, dev, [0] * len(fs))
-    t_s7 = _batch_ms(fs, prob.n_dual, dev, [7] * len(fs))
-    t_s5 = _batch_ms(fs, prob.n_dual, dev, [5] * len(fs))
-    print(f"batch ms: selected {t_sel:.2f}, all FP64 {t_fp64:.2f}, all 7-digit {t_s7:.2f}, all 5-digit {t_s5:.2f}; "
-          f"variants "
-          f"{dict(zip(*np.unique(var, return_counts=True)))}")
-    assert t_sel < t_fp64
-    assert t_sel <= 1.05 * min(t_s5, t_s7)        # no worse than the best uniform choice
+    uniform = {v: _batch_ms(fs, prob.n_dual, dev, [v] * len(fs)) for v in V}
+    print(f"batch ms: selected {t_sel:.2f}; uniform " + ", ".join(f"v{v} {t:.2f}" for v, t in uniform.items()) +
+          f"; variants {dict(zip(*np.unique(var, return_counts=True)))}")
+    assert t_sel < uniform[0]
+    assert t_sel <= 1.05 * min(uniform.values())     # no worse than the best uniform (digits, tile) choice
+    assert len(set(tune.tile(v) for v in var if v)) == 2 or len(set(var)) >= 2   # a real mix
