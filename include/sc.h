@@ -78,6 +78,12 @@ typedef enum {
  *   Bt_sign     -- [Bt_colptr[m]] int8, the entries of B_i^T (+1 or -1)
  *   lambda_map  -- [m] int32, local column -> global multiplier index
  *                  (used by sc_apply; may be NULL if sc_apply is never called)
+ *   Bt_val      -- optional [Bt_colptr[m]] double, finite: the entries of the
+ *                  right-hand side in place of Bt_sign (then NULL is allowed
+ *                  for Bt_sign); the same F = C^T (L L^T)^{-1} C is assembled
+ *                  for any sparse C, e.g. C = K_ib for the Schur complement
+ *                  K_bi K_ii^{-1} K_ib of a Dirichlet preconditioner
+ *                  (sc_plan only; sci_plan takes signed-Boolean columns)
  * Any number of nonzeros per column of B^T is accepted (general gluing); the
  * FETI case has exactly one. */
 typedef struct {
@@ -88,6 +94,7 @@ typedef struct {
   const int32_t *Bt_rowind;
   const int8_t *Bt_sign;
   const int32_t *lambda_map;
+  const double *Bt_val;
 } sc_subdomain_desc;
 
 enum { SC_FP64 = 0, SC_SPLIT_BF16 = 1 };
@@ -267,6 +274,16 @@ sc_status sc_apply(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, d
  * this library's. */
 sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
                          void *stream);
+
+/* The same product with the stored tiles split between GB300's two
+ * arithmetic paths so that both work at once: of every four tiles a warp
+ * visits, fp64_quarters (0..4) are multiplied in FP64 on the FP64 pipe (as
+ * sc_apply) and the rest in fixed point on the integer pipes (as
+ * sc_apply_fixed); each row and tile is rounded once either way, so the
+ * error bound is that of the two forms.  fp64_quarters = 0 is sc_apply_fixed.
+ * Same arguments, layout and asynchrony as sc_apply; q is overwritten. */
+sc_status sc_apply_mixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
+                         int32_t fp64_quarters, void *stream);
 
 /* Expand F_i into a dense full m_i x m_i column-major device matrix dst_dev
  * with leading dimension ld >= m_i.  Asynchronous on `stream`. */

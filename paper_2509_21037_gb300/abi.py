@@ -18,7 +18,7 @@ SC_OK, SC_ERR_INVALID_ARG, SC_ERR_NOT_SPD, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_TIMEO
 
 class SubdomainDesc(ctypes.Structure):
     _fields_ = [("n", c_i32), ("m", c_i32), ("L_colptr", c_vp), ("L_rowind", c_vp),
-                ("Bt_colptr", c_vp), ("Bt_rowind", c_vp), ("Bt_sign", c_vp), ("lambda_map", c_vp)]
+                ("Bt_colptr", c_vp), ("Bt_rowind", c_vp), ("Bt_sign", c_vp), ("lambda_map", c_vp), ("Bt_val", c_vp)]
 
 
 SC_FP64, SC_SPLIT_BF16 = 0, 1
@@ -66,6 +66,7 @@ SC_SYMBOLS = {
     "sc_assemble_batch_static": ([c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply_fixed": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_apply_mixed": ([c_vp, c_vp, c_vp, c_vp, c_i32, c_vp], c_int),
     "sc_export_F": ([c_vp, c_vp, c_i32, c_vp, c_i32, c_vp], c_int),
     "sc_enable_stage_timing": ([c_vp, c_i32], c_int),
     "sc_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), c_i32], c_int),

@@ -63,9 +63,12 @@ __device__ __forceinline__ void mac(long long &d0, long long &d1, long long &d2,
   d2 += (long long)m.y * l.y;
 }
 
+// fp64_quarters (0..4): of every four tiles a warp visits, this many are
+// multiplied in FP64 (FP64 pipe) and the rest in fixed point (integer pipes),
+// so that both pipes work at once; 0 is the pure fixed-point product.
 __global__ void __launch_bounds__(kThreads, 6) apply_fixed_kernel(const PlanPtrs P, const double *__restrict__ F,
                                                                const double *__restrict__ lam,
-                                                               double *__restrict__ q) {
+                                                               double *__restrict__ q, int fp64_quarters) {
   __shared__ double Ts[kThreads / 32][32][33];     // the tile, then its limbs in place
   __shared__ int2 LJ[kThreads / 32][32];           // limbs of the lambda block J
   __shared__ int2 LI[kThreads / 32][32];           // limbs of the lambda block I
@@ -95,6 +98,19 @@ __global__ void __launch_bounds__(kThreads, 6) apply_fixed_kernel(const PlanPtrs
     const uint32_t exT = __reduce_max_sync(kFull, em);
     const int colJ = J * kTile + lane;
     const double pJ = colJ < sd.m ? lam[map[colJ]] : 0.0;
+    if (((J >> 2) + J) % 4 < fp64_quarters) {     // this tile on the FP64 pipe (uniform across the warp)
+      __syncwarp();
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) y = fma(Ts[warp][c][lane], __shfl_sync(kFull, pJ, c), y);
+      if (J < I) {
+        double z = 0.0;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) z = fma(Ts[warp][lane][r], __shfl_sync(kFull, pI, r), z);
+        if (colJ < sd.m) atomicAdd(q + map[colJ], z);
+      }
+      __syncwarp();
+      continue;
+    }
     const uint32_t exJ = __reduce_max_sync(kFull, exp_field(pJ));
     if (exT == 0) continue;                        // an all-zero tile adds nothing (uniform)
     // each lane converts the entries it staged, in place
@@ -130,13 +146,16 @@ __global__ void __launch_bounds__(kThreads, 6) apply_fixed_kernel(const PlanPtrs
 
 }  // namespace
 
-extern "C" sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
-                                    void *stream) {
+namespace {
+
+sc_status apply_split(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev, int fp64_quarters,
+                      void *stream, const char *who) {
   if (!ctx) return SC_ERR_INVALID_ARG;
   if (!ctx->plan_dev && !ctx->blob.empty()) return fail(ctx, SC_ERR_STATE, "sc_upload_plan was not called");
   if (!ctx->has_lambda) return fail(ctx, SC_ERR_STATE, "planned without lambda_map");
   if (ctx->n_dual > 0 && (!lambda_dev || !q_dev)) return fail(ctx, SC_ERR_INVALID_ARG, "lambda_dev or q_dev is NULL");
   if (ctx->sizes.F_doubles > 0 && !F_dev) return fail(ctx, SC_ERR_INVALID_ARG, "F_dev is NULL");
+  if (fp64_quarters < 0 || fp64_quarters > 4) return fail(ctx, SC_ERR_INVALID_ARG, "fp64_quarters must be 0..4");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (ctx->n_dual > 0) e = cudaMemsetAsync(q_dev, 0, sizeof(double) * (size_t)ctx->n_dual, st);
@@ -145,9 +164,22 @@ extern "C" sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const doub
     e = cudaFuncSetAttribute(apply_fixed_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && ctx->n_apply > 0) {
-    apply_fixed_kernel<<<(unsigned)ctx->n_apply, kThreads, 0, st>>>(ctx->ptrs(), F_dev, lambda_dev, q_dev);
+    apply_fixed_kernel<<<(unsigned)ctx->n_apply, kThreads, 0, st>>>(ctx->ptrs(), F_dev, lambda_dev, q_dev,
+                                                                     fp64_quarters);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) return fail(ctx, SC_ERR_CUDA, std::string("sc_apply_fixed: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(ctx, SC_ERR_CUDA, std::string(who) + ": " + cudaGetErrorString(e));
   return SC_OK;
+}
+
+}  // namespace
+
+extern "C" sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
+                                    void *stream) {
+  return apply_split(ctx, F_dev, lambda_dev, q_dev, 0, stream, "sc_apply_fixed");
+}
+
+extern "C" sc_status sc_apply_mixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
+                                    int32_t fp64_quarters, void *stream) {
+  return apply_split(ctx, F_dev, lambda_dev, q_dev, fp64_quarters, stream, "sc_apply_mixed");
 }

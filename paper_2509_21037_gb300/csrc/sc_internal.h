@@ -224,8 +224,9 @@ int launch_lpack_split(const sc_ctx &c, int S, int64_t base, int64_t count, cons
 int launch_trsm_split(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Lv, const double *invd,
                       void *ws, double *Y, void *stream);
 int launch_colexp_reset(const sc_ctx &c, void *ws, void *stream);
+// balanced: digits in [-128, 128] against twice the column bound (the tcgen05 SYRK's planes)
 int launch_yslice_group(const sc_ctx &c, int S, int64_t base, int64_t count, const double *Y, void *ws,
-                        void *stream);
+                        void *stream, bool balanced);
 int launch_syrk_split(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);
 // the 128x32-tile SYRK on tcgen05 (sc_syrk_tc.cu); tc_smem_bytes: its dynamic shared memory
 int launch_syrk_tc(const sc_ctx &c, int S, int64_t base, int64_t count, void *ws, double *F, void *stream);

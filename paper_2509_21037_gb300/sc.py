@@ -51,6 +51,11 @@ class Plan:
             d.n, d.m = fs.n, fs.m
             d.L_colptr, d.L_rowind, d.Bt_colptr, d.Bt_rowind, d.Bt_sign, d.lambda_map = \
                 [a.ctypes.data if a.size else None for a in arrs]
+            bv = getattr(fs, "bt_val", None)
+            if bv is not None:
+                bv = np.ascontiguousarray(bv, np.float64)
+                keep.append(bv)
+                d.Bt_val = bv.ctypes.data if bv.size else None
         h = ctypes.c_void_p()
         opt = abi.Options()
         opt.precision = precision
@@ -128,6 +133,12 @@ class Plan:
     def apply_fixed(self, F, lam, q, stream=None):
         """q = F * lambda on the integer pipes (include/sc.h, sc_apply_fixed)."""
         self._check(self.lib.sc_apply_fixed(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(),
+                                            _stream_ptr(stream)))
+
+    def apply_mixed(self, F, lam, q, fp64_quarters: int = 2, stream=None):
+        """q = F * lambda with the tiles split between the FP64 pipe and the
+        integer pipes (include/sc.h, sc_apply_mixed)."""
+        self._check(self.lib.sc_apply_mixed(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(), int(fp64_quarters),
                                             _stream_ptr(stream)))
 
     def export(self, F, i: int, dst=None, stream=None):

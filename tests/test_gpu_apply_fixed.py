@@ -73,3 +73,27 @@ def test_apply_fixed_config2_and_dynamic_range(dev):
         # undo the power-of-two scale before the norms (their squares would leave the FP64 range)
         assert _rel(_q(plan, Fs, lam, dev) / s, q64) <= 1e-14
     assert np.all(_q(plan, F, np.zeros(prob.n_dual), dev) == 0.0)
+
+
+@pytest.mark.parametrize("quarters", [0, 1, 2, 3, 4])
+def test_apply_mixed_every_split(quarters, dev):
+    """sc_apply_mixed: of every four tiles `quarters` run on the FP64 pipe and
+    the rest in fixed point.  Against the oracle (1e-12) and the FP64 apply
+    (1e-14) for every split, on a mixed batch whose subdomains have 1..many
+    tile columns; quarters = 0 is sc_apply_fixed (the same kernel; q's
+    atomic accumulation order differs run to run, so to rounding)."""
+    prob = synth.mixed_batch(lat2d=(2, 2), k2d=(6, 40), lat3d=(2, 1, 1), k3d=(2, 5), seed=1)
+    plan, F = _setup(prob, dev)
+    lam = np.random.default_rng(3).standard_normal(prob.n_dual)
+    lam_d = torch.from_numpy(lam).to(dev)
+    q = torch.full_like(lam_d, float("nan"))
+    plan.apply_mixed(F, lam_d, q, quarters)
+    qm = q.cpu().numpy()
+    q64 = _q(plan, F, lam, dev, fixed=False)
+    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains, refine=1), [s.lambda_map for s in prob.subdomains],
+                           lam, prob.n_dual)
+    assert _rel(qm, qo) <= 1e-12 and _rel(qm, q64) <= 1e-14
+    if quarters == 0:
+        assert _rel(qm, _q(plan, F, lam, dev)) <= 1e-15
+    with pytest.raises(sc.SCError):
+        plan.apply_mixed(F, lam_d, q, 5)
