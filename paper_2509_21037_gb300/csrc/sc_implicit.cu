@@ -468,6 +468,9 @@ sc_status ifail(sci_ctx *c, sc_status st, const std::string &m) {
 }
 
 sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t cluster_min_work) {
+  for (int32_t i = 0; i < nsub; ++i)
+    if (d[i].Bt_val)
+      return ifail(ctx, SC_ERR_INVALID_ARG, "subdomain " + std::to_string(i) + ": sci_plan takes signed-Boolean B^T (Bt_val must be NULL)");
   std::vector<ISub> subs;
   std::vector<ISn> sns;
   std::vector<int32_t> levptr, rows;

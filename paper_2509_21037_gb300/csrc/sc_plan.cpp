@@ -76,7 +76,7 @@ std::string sc::analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
   if (n < 0 || m < 0) return sub_msg(idx, "negative n or m");
   if (n == 0 && m > 0) return sub_msg(idx, "m > 0 with n == 0");
   if (n > 0 && (!d.L_colptr || !d.L_rowind)) return sub_msg(idx, "L pattern pointers are NULL");
-  if (m > 0 && (!d.Bt_colptr || !d.Bt_rowind || !d.Bt_sign)) return sub_msg(idx, "B^T pointers are NULL");
+  if (m > 0 && (!d.Bt_colptr || !d.Bt_rowind || (!d.Bt_sign && !d.Bt_val))) return sub_msg(idx, "B^T pointers are NULL");
   const int64_t *cp = d.L_colptr;
   const int32_t *ri = d.L_rowind;
   if (n > 0 && cp[0] != 0) return sub_msg(idx, "L_colptr[0] != 0");
@@ -96,7 +96,11 @@ std::string sc::analyze(int32_t idx, const sc_subdomain_desc &d, SubPlan &P) {
         if (d.Bt_rowind[e] < 0 || d.Bt_rowind[e] >= n) return sub_msg(idx, "B^T row out of range");
         if (e > d.Bt_colptr[j] && d.Bt_rowind[e] <= d.Bt_rowind[e - 1])
           return sub_msg(idx, "B^T rows not strictly ascending in column " + std::to_string(j));
-        if (d.Bt_sign[e] != 1 && d.Bt_sign[e] != -1) return sub_msg(idx, "B^T entry is not +1/-1");
+        if (d.Bt_val) {
+          if (!std::isfinite(d.Bt_val[e])) return sub_msg(idx, "B^T value is not finite");
+        } else if (d.Bt_sign[e] != 1 && d.Bt_sign[e] != -1) {
+          return sub_msg(idx, "B^T entry is not +1/-1");
+        }
       }
     }
   }
@@ -381,7 +385,7 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
         int32_t ws = S.sn_jhi[s] - S.sn_jlo[s];
         Seed sdd;
         sdd.y_off = yoff[s] + (int64_t)(r - S.sn_c0[s]) * ws + (q - S.sn_jlo[s]);
-        sdd.value = (double)D.Bt_sign[e];
+        sdd.value = D.Bt_val ? D.Bt_val[e] : (double)D.Bt_sign[e];
         seeds.push_back(sdd);
       }
     }

@@ -146,6 +146,87 @@ def dirichlet_block(sd, S: Optional[np.ndarray] = None) -> np.ndarray:
     return 0.5 * (P + P.T)
 
 
+def dirichlet_problem(subdomains, threads: int = 0):
+    """The Dirichlet preconditioner's blocks B_i S_i B_i^T as this library's
+    problem (host part of ``dirichlet_operator_gpu``):
+
+        B_i S_i B_i^T = B_b K_bb B_b^T - C_i^T K_ii^{-1} C_i,   C_i = K_ib B_b^T,
+
+    returns, per subdomain, the library input for the second term -- the
+    sparse Cholesky factor of the interior block K_ii (nested-dissection order
+    restricted to the interior dofs, once per distinct (K_i, glued dofs) pair)
+    and the general right-hand side C_i in its order (column j: s_j times the
+    coupling column K_ib of multiplier j's dof; include/sc.h Bt_val) -- and
+    the dense first term B_b K_bb B_b^T in the local multiplier order."""
+    cache = {}
+    todo = []
+    keys = []
+    for sd in subdomains:
+        b = glued_dofs(sd)
+        key = (sd.key, b.tobytes()) if sd.key is not None else id(sd)
+        keys.append((key, b))
+        if key not in cache:
+            cache[key] = None
+            todo.append((key, sd, b))
+
+    def interior_factor(item):
+        key, sd, b = item
+        n = sd.K.shape[0]
+        K = sp.csr_matrix(sd.K)
+        inner = np.setdiff1d(np.arange(n), b)
+        pos = np.full(n, -1, np.int64)
+        pos[inner] = np.arange(len(inner))
+        order = pos[host.nested_dissection(sd.grid, sd.ndpn)]
+        order = order[order >= 0].astype(np.int32)
+        L = host.factorize(K[inner][:, inner], [], order, postorder=True)
+        return key, (L, sp.csc_matrix(K[inner][:, b]), K[b][:, b].toarray())
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads or None) as ex:
+        for key, val in ex.map(interior_factor, todo):
+            cache[key] = val
+    facs, kbb = [], []
+    for sd, (key, b) in zip(subdomains, keys):
+        L, Kib, Kbb = cache[key]
+        Bt = sp.csc_matrix(sd.Bt)
+        if not np.all(np.diff(Bt.indptr) == 1):
+            raise ValueError("the Dirichlet set-up through the library assumes one nonzero per B^T column")
+        d, sg = Bt.indices, np.sign(Bt.data)
+        pb = np.searchsorted(b, d)
+        C = sp.csc_matrix(Kib[:, pb] @ sp.diags(sg))            # n_inner x m, column j = s_j K_ib[:, d_j]
+        C.eliminate_zeros()
+        rows = L.iperm[C.indices]
+        cp = C.indptr.astype(np.int32)
+        colof = np.repeat(np.arange(C.shape[1]), np.diff(C.indptr))
+        o = np.lexsort((rows, colof))                           # rows ascending in L's order, per column
+        ri, vals = rows[o], C.data[o]
+        facs.append(host.FactoredSubdomain(L, cp, ri.astype(np.int32), np.ones(len(ri), np.int8),
+                                           np.asarray(sd.lambda_map, np.int32), vals))
+        kbb.append(sg[:, None] * Kbb[np.ix_(pb, pb)] * sg[None, :])
+    return facs, kbb
+
+
+def dirichlet_operator_gpu(subdomains, plan, device, threads: int = 0):
+    """sum_i B_i S_i B_i^T tile-packed in ``plan``'s F layout, its Schur
+    complements assembled on the GPU by this library (``dirichlet_problem``:
+    the interior factors and coupling columns, then sc_assemble_batch for
+    C_i^T K_ii^{-1} C_i, subtracted from the packed K_bb blocks).  Returns
+    (buffer, set-up seconds)."""
+    import torch
+    t0 = time.perf_counter()
+    facs, kbb = dirichlet_problem(subdomains, threads)
+    splan = sc.Plan(facs, max(1, int(plan.n_dual))).upload(device)
+    Fc = splan.new_F(device)
+    splan.assemble(torch.from_numpy(sc.concat_L_values(facs)).to(device), Fc)
+    if splan.device_status() != 0:
+        raise RuntimeError("interior factor of a Dirichlet Schur complement is not SPD")
+    if not np.array_equal(splan.F_offsets, plan.F_offsets):
+        raise RuntimeError("F layouts differ")
+    M = plan.pack(kbb, device) - Fc
+    torch.cuda.synchronize(device)
+    return M, time.perf_counter() - t0
+
+
 class _KPlus:
     """x = K^+ b for one subdomain with its host factor: K_reg^{-1} b (two
     host triangular solves, scf_solve) with the fixed dofs zeroed."""
@@ -180,14 +261,16 @@ class FETISolver:
     """PCPG on the dual interface problem with the assembled F on the GPU.
 
     precond: "lumped" (sum_i B_i K_i B_i^T), "dirichlet" (sum_i B_i S_i B_i^T,
-    applied with the library's sc_apply on a tile-packed copy) or "none";
+    applied with the library's sc_apply on a tile-packed copy; set up on the
+    GPU by the library's own assembly with dirichlet_setup "gpu", the default
+    on a CUDA device, or by dense host Cholesky with "host") or "none";
     scaling: "bbt" (W M W, W = (B B^T)^+) or "none" (M alone).
-    ``precond_setup_s`` is the host time of the Dirichlet Schur complements
-    (one per distinct (K_i, glued dofs) pair).
+    ``precond_setup_s`` is the wall time of the Dirichlet preconditioner's
+    set-up (host work once per distinct (K_i, glued dofs) pair).
     """
 
     def __init__(self, problem, factored: Optional[Sequence] = None, device="cuda", precond: str = "lumped",
-                 plan_kwargs: Optional[dict] = None, scaling: str = "bbt"):
+                 plan_kwargs: Optional[dict] = None, scaling: str = "bbt", dirichlet_setup: str = "auto"):
         import torch
         if precond not in ("lumped", "dirichlet", "none"):
             raise ValueError(f"unknown preconditioner {precond!r}")
@@ -226,19 +309,24 @@ class FETISolver:
         self.q = torch.empty(self.nd, dtype=torch.float64, device=self.dev)
         self.Mdir, self.precond_setup_s = None, 0.0
         if precond == "dirichlet":
-            t0 = time.perf_counter()
-            cache = {}
-            blocks = []
-            for sd in subs:
-                key = None if sd.key is None else (sd.key, glued_dofs(sd).tobytes())
-                S = cache.get(key) if key is not None else None
-                if S is None:
-                    S = schur_on_glued(sd)
-                    if key is not None:
-                        cache[key] = S
-                blocks.append(dirichlet_block(sd, S))
-            self.precond_setup_s = time.perf_counter() - t0
-            self.Mdir = self.plan.pack(blocks, self.dev)
+            if dirichlet_setup not in ("auto", "gpu", "host"):
+                raise ValueError(f"unknown Dirichlet set-up {dirichlet_setup!r}")
+            if dirichlet_setup == "gpu" or (dirichlet_setup == "auto" and self.dev.type == "cuda"):
+                self.Mdir, self.precond_setup_s = dirichlet_operator_gpu(subs, self.plan, self.dev)
+            else:
+                t0 = time.perf_counter()
+                cache = {}
+                blocks = []
+                for sd in subs:
+                    key = None if sd.key is None else (sd.key, glued_dofs(sd).tobytes())
+                    S = cache.get(key) if key is not None else None
+                    if S is None:
+                        S = schur_on_glued(sd)
+                        if key is not None:
+                            cache[key] = S
+                    blocks.append(dirichlet_block(sd, S))
+                self.precond_setup_s = time.perf_counter() - t0
+                self.Mdir = self.plan.pack(blocks, self.dev)
             self.qz = torch.empty(self.nd, dtype=torch.float64, device=self.dev)
         self.W = None
         if precond != "none" and scaling == "bbt":

@@ -191,6 +191,7 @@ class FactoredSubdomain:
     bt_rowind: np.ndarray   # int32 [nnz(B^T)], rows in L's ordering
     bt_sign: np.ndarray     # int8  [nnz(B^T)]
     lambda_map: np.ndarray  # int32 [m]
+    bt_val: Optional[np.ndarray] = None   # float64 [nnz(B^T)]: general values in place of bt_sign
 
     @property
     def n(self) -> int:

@@ -77,6 +77,40 @@ int main(void) {
   sc_destroy(ctx);
   d.L_rowind = rowind;
 
+  /* the options added to sc_options (tile, sub_tile, poll_limit) are validated on the host */
+  {
+    sc_options o2;
+    memset(&o2, 0, sizeof o2);
+    o2.precision = SC_SPLIT_BF16;
+    o2.n_slices = 5;
+    o2.tile = SC_TILE_TC128;
+    o2.poll_limit = 1000;
+    CHECK(sc_plan(&ctx, 1, &d, 2, &o2) == SC_OK, sc_last_error(ctx));
+    float feat[SC_NUM_FEATURES];
+    CHECK(sc_subdomain_features(ctx, NULL, feat) == SC_OK && feat[0] > 0.f && feat[9] == 0.f, "features");
+    sc_destroy(ctx);
+    const int8_t bad_tile[1] = {2};
+    o2.sub_tile = bad_tile;
+    CHECK(sc_plan(&ctx, 1, &d, 2, &o2) == SC_ERR_INVALID_ARG, "sub_tile 2 accepted");
+    sc_destroy(ctx);
+    o2.sub_tile = NULL;
+    o2.poll_limit = -1;
+    CHECK(sc_plan(&ctx, 1, &d, 2, &o2) == SC_ERR_INVALID_ARG, "negative poll_limit accepted");
+    sc_destroy(ctx);
+    /* general B^T values in place of the signs */
+    const double bt_val[2] = {0.5, -3.0};
+    sc_subdomain_desc dv = d;
+    dv.Bt_sign = NULL;
+    dv.Bt_val = bt_val;
+    CHECK(sc_plan(&ctx, 1, &dv, 2, NULL) == SC_OK, sc_last_error(ctx));
+    sc_destroy(ctx);
+    const double bt_nan[2] = {0.5, NAN};
+    dv.Bt_val = bt_nan;
+    CHECK(sc_plan(&ctx, 1, &dv, 2, NULL) == SC_ERR_INVALID_ARG, "non-finite B^T value accepted");
+    sc_destroy(ctx);
+    ctx = NULL;
+  }
+
   sci_ctx *ic = NULL;
   CHECK(sci_plan(&ic, 1, &d, 2, NULL) == SC_OK, sci_last_error(ic));
   sci_sizes is;

@@ -84,7 +84,7 @@ def check_bounds(T: dict, sizes, stats, tile_subs=()) -> None:
             base = T["rmap"][s["rmap_off"] + k]
             assert 0 <= base and base + ws <= ydbl
     for e in T["seeds"]:
-        assert 0 <= e["y_off"] < ydbl and e["value"] in (-1.0, 1.0)
+        assert 0 <= e["y_off"] < ydbl and np.isfinite(e["value"]) and e["value"] != 0.0
     for t in T["trsm"]:
         sd = subs[t["sub"]]
         assert 0 < t["w"] <= 32 and t["c_lo"] + t["w"] <= sd["m"]

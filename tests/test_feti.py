@@ -244,3 +244,23 @@ def test_feti_solver_logic_on_the_cpu():
         assert r.continuity <= 1e-8 and r.equilibrium <= 1e-8
         its[pc] = r.iterations
     assert its["dirichlet"] < its["lumped"] < its["none"], its
+
+
+def test_dirichlet_blocks_through_the_library_plan():
+    """The Dirichlet preconditioner's blocks as this library's problem
+    (interior factor + general right-hand side C_i = K_ib B_b^T, include/sc.h
+    Bt_val): the plan replayed on the CPU gives C_i^T K_ii^{-1} C_i, and
+    K_bb's gather minus it equals the dense host Schur complement
+    (schur_on_glued / dirichlet_block) block by block."""
+    import plan_emulator as pe
+    from paper_2509_21037_gb300 import sc
+    for prob in (synth.cube_heat_3d(parts=2, k=4), synth.elasticity_cubes((2, 2, 1), 2, 3, seed=1)):
+        facs, kbb = feti.dirichlet_problem(prob.subdomains, threads=1)
+        plan = sc.Plan(facs, prob.n_dual)
+        T = pe.export_plan(plan)
+        pe.check_bounds(T, plan.sizes, plan.stats)
+        Fc = pe.emulate_assembly(T, plan.sizes, plan.stats, sc.concat_L_values(facs))
+        for i, sd in enumerate(prob.subdomains):
+            M = kbb[i] - pe.export_dense(T, Fc, i)
+            ref = feti.dirichlet_block(sd)
+            assert np.linalg.norm(M - ref) <= 1e-12 * np.linalg.norm(ref), i
