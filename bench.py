@@ -364,7 +364,8 @@ def run_sc(args):
     fs = host.factorize_problem(prob.subdomains)
     if args.profile and args.profile_slices:
         from paper_2509_21037_gb300 import abi
-        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=args.profile_slices).upload(dev)
+        plan = sc.Plan(fs, prob.n_dual, precision=abi.SC_SPLIT_BF16, n_slices=args.profile_slices,
+                       tile=args.profile_tile).upload(dev)
     else:
         plan = sc.Plan(fs, prob.n_dual).upload(dev)
     Lh = sc.concat_L_values(fs)
@@ -417,6 +418,8 @@ def run_sc(args):
     if args.profile:
         for _ in range(args.warmup + args.steps):
             plan.apply_fixed(F, lam, q, stream)
+        for _ in range(args.warmup + args.steps):
+            plan.apply_mixed(F, lam, q, args.profile_mixed, stream)
         torch.cuda.synchronize(dev)
         if args.profile_implicit:
             from paper_2509_21037_gb300 import implicit
@@ -514,8 +517,25 @@ def run_sc(args):
     a1.record(stream)
     a1.synchronize()
     t_fixed = a0.elapsed_time(a1) / 20
+    # the tiles split between the FP64 pipe and the integer pipes (sc_apply_mixed): every share
+    mixed = {}
+    qm = torch.empty_like(q)
+    for quarters in (1, 2, 3):
+        plan.apply_mixed(F, lam, qm, quarters, stream)
+        a0.record(stream)
+        for _ in range(20):
+            plan.apply_mixed(F, lam, qm, quarters, stream)
+        a1.record(stream)
+        a1.synchronize()
+        tm = a0.elapsed_time(a1) / 20
+        mixed[str(quarters)] = {"ms": tm, "GBps": st["bytes_apply"] / (tm / 1e3) / 1e9,
+                                "frac_hbm": st["bytes_apply"] / (tm / 1e3) / 1e9 / HBM_PEAK_GBPS,
+                                "rel_diff_vs_fp64": (torch.linalg.vector_norm(qm - q) /
+                                                     torch.linalg.vector_norm(q)).item()}
+    best_q = min(mixed, key=lambda k: mixed[k]["ms"])
     apply_sec = {
         "bytes": st["bytes_apply"],
+        "mixed": {"best_fp64_quarters": int(best_q), **mixed[best_q], "by_fp64_quarters": mixed},
         "fp64": {"ms": t_expl, "GBps": st["bytes_apply"] / (t_expl / 1e3) / 1e9,
                  "frac_hbm": st["bytes_apply"] / (t_expl / 1e3) / 1e9 / HBM_PEAK_GBPS},
         "fixed": {"ms": t_fixed, "GBps": st["bytes_apply"] / (t_fixed / 1e3) / 1e9,
@@ -719,7 +739,7 @@ def run_config5(args):
     t_prep = time.time() - t0
     Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
     lam = torch.from_numpy(np.random.default_rng(args.seed).standard_normal(prob.n_dual)).to(dev)
-    V = (0, 7, 5)
+    V = tune.VARIANTS
     keys = sorted({tune.class_key(f) for f in fs}, key=lambda k: (k[0], k[2], k[1]))
     train = keys[::3]
     t1 = time.time()
@@ -729,8 +749,8 @@ def run_config5(args):
     sel.fit(list(recs.values()), epochs=3000)
     var = tune.select(fs, args.tol, sel, measured=recs)
 
-    def timed(sub_slices, ws_limit, keep_F=False):
-        plan = sc.Plan(fs, prob.n_dual, sub_slices=sub_slices, ws_limit=ws_limit).upload(dev)
+    def timed(var_codes, ws_limit, keep_F=False):
+        plan = sc.Plan(fs, prob.n_dual, ws_limit=ws_limit, **tune.plan_options(var_codes)).upload(dev)
         F = plan.new_F(dev)
         q = torch.empty_like(lam)
         plan.assemble(Lv, F)
@@ -841,6 +861,10 @@ def main():
     ap.add_argument("--ws-limit-gb", type=float, default=48.0, help="config 5: workspace bound per wave")
     ap.add_argument("--profile-slices", type=int, default=0,
                     help="with --profile: run the split-precision variant with this many slices")
+    ap.add_argument("--profile-tile", type=int, default=0, choices=[0, 1],
+                    help="with --profile-slices: SYRK tile (0 = 32x32 mma.sync, 1 = 128x32 tcgen05)")
+    ap.add_argument("--profile-mixed", type=int, default=2, choices=[0, 1, 2, 3, 4],
+                    help="with --profile: sc_apply_mixed's FP64 share (quarters of the tiles)")
     ap.add_argument("--profile-implicit", action="store_true",
                     help="with --profile: also run the GPU implicit apply warmup + steps times")
     ap.add_argument("--profile", action="store_true",
