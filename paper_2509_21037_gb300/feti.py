@@ -169,6 +169,11 @@ def dirichlet_problem(subdomains, threads: int = 0):
             cache[key] = None
             todo.append((key, sd, b))
 
+    nd_cache = {}
+    for _, sd, _ in todo:                       # one ordering per grid shape (deterministic)
+        if (tuple(sd.grid), sd.ndpn) not in nd_cache:
+            nd_cache[(tuple(sd.grid), sd.ndpn)] = host.nested_dissection(sd.grid, sd.ndpn)
+
     def interior_factor(item):
         key, sd, b = item
         n = sd.K.shape[0]
@@ -176,7 +181,7 @@ def dirichlet_problem(subdomains, threads: int = 0):
         inner = np.setdiff1d(np.arange(n), b)
         pos = np.full(n, -1, np.int64)
         pos[inner] = np.arange(len(inner))
-        order = pos[host.nested_dissection(sd.grid, sd.ndpn)]
+        order = pos[nd_cache[(tuple(sd.grid), sd.ndpn)]]
         order = order[order >= 0].astype(np.int32)
         L = host.factorize(K[inner][:, inner], [], order, postorder=True)
         return key, (L, sp.csc_matrix(K[inner][:, b]), K[b][:, b].toarray())
@@ -270,7 +275,8 @@ class FETISolver:
     """
 
     def __init__(self, problem, factored: Optional[Sequence] = None, device="cuda", precond: str = "lumped",
-                 plan_kwargs: Optional[dict] = None, scaling: str = "bbt", dirichlet_setup: str = "auto"):
+                 plan_kwargs: Optional[dict] = None, scaling: str = "bbt", dirichlet_setup: str = "auto",
+                 apply: str = "auto", check_every: int = 4):
         import torch
         if precond not in ("lumped", "dirichlet", "none"):
             raise ValueError(f"unknown preconditioner {precond!r}")
@@ -278,6 +284,12 @@ class FETISolver:
             raise ValueError(f"unknown scaling {scaling!r}")
         self.torch = torch
         self.dev = torch.device(device)
+        if apply not in ("auto", "fp64", "mixed"):
+            raise ValueError(f"unknown apply {apply!r}")
+        # the operator applies: "mixed" (sc_apply_mixed) on a CUDA device by default
+        self.apply_mode = ("mixed" if self.dev.type == "cuda" else "fp64") if apply == "auto" else apply
+        self.apply_fp64_quarters = 1
+        self.check_every = max(1, int(check_every))
         subs = problem.subdomains
         self.subs = subs
         self.nd = int(problem.n_dual)
@@ -371,9 +383,18 @@ class FETISolver:
         return t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd),
                                    check_invariants=True).coalesce().to(self.dev)
 
+    def _apply(self, M, x, out):
+        """out = M x for a tile-packed operator of the plan's layout: the
+        library's FP64 apply, or (apply="mixed") the tiles split between the
+        FP64 pipe and the integer pipes (sc_apply_mixed, same error bound)."""
+        if self.apply_mode == "mixed":
+            self.plan.apply_mixed(M, x, out, self.apply_fp64_quarters)
+        else:
+            self.plan.apply(M, x, out)
+
     def apply_F(self, x):
-        """q = F x (library sc_apply, then the fixed-dof correction)."""
-        self.plan.apply(self.F, x, self.q)
+        """q = F x (library apply, then the fixed-dof correction)."""
+        self._apply(self.F, x, self.q)
         return self.q - self.torch.sparse.mm(self.C, x[:, None])[:, 0]
 
     def project(self, x):
@@ -389,7 +410,7 @@ class FETISolver:
         if self.M is not None:
             y = t.sparse.mm(self.M, x[:, None])[:, 0]
         else:
-            self.plan.apply(self.Mdir, x.contiguous(), self.qz)
+            self._apply(self.Mdir, x.contiguous(), self.qz)
             y = self.qz
         if self.W is not None:
             y = t.sparse.mm(self.W, y[:, None])[:, 0]
@@ -397,7 +418,9 @@ class FETISolver:
 
     def solve(self, loads: Sequence[np.ndarray], tol: float = 1e-10, maxit: int = 1000,
               recover: bool = True) -> FETIResult:
-        """PCPG to ||w_k|| / ||w_0|| < tol.  recover=False skips the primal
+        """PCPG to ||w_k|| / ||w_0|| < tol (read every ``check_every``
+        iterations: the loop may run up to check_every - 1 iterations past the
+        first one below tol, which is the one reported).  recover=False skips the primal
         recovery and its checks (alpha, u, continuity and equilibrium are
         then empty or NaN): a solve for the iteration count or the time."""
         t = self.torch
@@ -411,6 +434,10 @@ class FETISolver:
         w0 = t.linalg.vector_norm(w).item()
         res, p, zw_old, it = [1.0], None, None, 0
         if w0 > 0:
+            # the scalars stay on the device; the host reads the residual norms
+            # every check_every iterations (one synchronisation instead of one
+            # per iteration), so the GPU runs ahead of the loop in between
+            pending = []
             for it in range(1, maxit + 1):
                 z = self.precondition(w)
                 zw = t.dot(z, w)
@@ -421,9 +448,18 @@ class FETISolver:
                 r = r - eta * qv
                 w = self.project(r)
                 zw_old = zw
-                res.append(t.linalg.vector_norm(w).item() / w0)
-                if res[-1] < tol:
-                    break
+                pending.append(t.linalg.vector_norm(w))
+                if it % self.check_every == 0 or it == maxit:
+                    vals = t.stack(pending).cpu().numpy() / w0
+                    pending = []
+                    hit = np.nonzero(vals < tol)[0]
+                    if len(hit):
+                        # the first iterate below tol is where the per-iteration loop would have stopped;
+                        # the few extra iterations only refine lambda further
+                        res.extend(vals[:hit[0] + 1].tolist())
+                        it = it - (len(vals) - 1 - hit[0])
+                        break
+                    res.extend(vals.tolist())
         ev1.record()
         ev1.synchronize()
         solve_ms = ev0.elapsed_time(ev1)
