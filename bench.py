@@ -68,6 +68,17 @@ def _measured_bf16_tflops() -> float:
 BF16_PEAK_TFLOPS = _measured_bf16_tflops()
 
 
+def _json_default(o):
+    """numpy scalars and arrays in the JSON line (a type the encoder does not know must not end the run)."""
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, np.floating):
+        return float(o)
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    return str(o)
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -230,7 +241,7 @@ def run_reference(args):
                                        f"distinct K, then forward/backward substitution on the B^T dofs)",
                              "unmemoised": _oracle_unmemoised(prob)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps(line, default=_json_default))
     return 0
 
 
@@ -659,7 +670,7 @@ def run_sc(args):
                                 "sample": f"first {S} of 64 subdomains, fresh memo, FP64 dense Cholesky + solves + one refinement step",
                                 "unmemoised": _oracle_unmemoised(prob)}
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, default=_json_default))
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -833,7 +844,7 @@ def run_config5(args):
         "autotune": {"classes_measured": len(recs), "classes_total": len(keys), "seconds": t_tune},
         "host_factorisation_s": t_prep,
     }
-    print(json.dumps(line))
+    print(json.dumps(line, default=_json_default))
     return 0
 
 

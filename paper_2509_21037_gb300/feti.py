@@ -457,7 +457,7 @@ class FETISolver:
                         # the first iterate below tol is where the per-iteration loop would have stopped;
                         # the few extra iterations only refine lambda further
                         res.extend(vals[:hit[0] + 1].tolist())
-                        it = it - (len(vals) - 1 - hit[0])
+                        it = int(it - (len(vals) - 1 - hit[0]))
                         break
                     res.extend(vals.tolist())
         ev1.record()
