@@ -49,9 +49,13 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kWarps = 8;
+// 16 warps per CTA and one CTA per SM: a subdomain that a CTA solves alone
+// gets twice the warps for the wide lower levels of its elimination tree
+// (many small supernodes, one warp each), where the solve spends most of
+// its time when there are fewer subdomains than SMs
+constexpr int kWarps = 16;
 constexpr int kCluster = 8;     // CTAs per cluster (portable maximum)
-constexpr int64_t kCtaSlots = 152 * 2;   // resident CTAs on a GB300 (152 SMs, 2 CTAs each)
+constexpr int64_t kCtaSlots = 152;   // resident CTAs on a GB300 (152 SMs, 1 CTA each)
 constexpr int kThreadsI = 32 * kWarps;
 constexpr uint32_t kFull = 0xffffffffu;
 
@@ -403,7 +407,7 @@ __device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, 
 // Launched in clusters of kCluster CTAs.  An item is either one large
 // subdomain solved by the whole cluster, or up to kCluster small subdomains,
 // one per CTA.
-__global__ void __launch_bounds__(kThreadsI, 2) implicit_kernel(const IPtrs P, const double *__restrict__ Lv,
+__global__ void __launch_bounds__(kThreadsI, 1) implicit_kernel(const IPtrs P, const double *__restrict__ Lv,
                                                                 const double *__restrict__ lam, double *q,
                                                                 double *X, uint32_t *status) {
   __shared__ double ys[kWarps][32];

@@ -220,16 +220,22 @@ def dirichlet_operator_gpu(subdomains, plan, device, threads: int = 0):
     import torch
     t0 = time.perf_counter()
     facs, kbb = dirichlet_problem(subdomains, threads)
+    t1 = time.perf_counter()
     splan = sc.Plan(facs, max(1, int(plan.n_dual))).upload(device)
+    t2 = time.perf_counter()
     Fc = splan.new_F(device)
     splan.assemble(torch.from_numpy(sc.concat_L_values(facs)).to(device), Fc)
     if splan.device_status() != 0:
         raise RuntimeError("interior factor of a Dirichlet Schur complement is not SPD")
     if not np.array_equal(splan.F_offsets, plan.F_offsets):
         raise RuntimeError("F layouts differ")
+    t3 = time.perf_counter()
     M = plan.pack(kbb, device) - Fc
     torch.cuda.synchronize(device)
-    return M, time.perf_counter() - t0
+    t4 = time.perf_counter()
+    dirichlet_operator_gpu.last_breakdown = {"host_factors_and_coupling_s": t1 - t0, "plan_s": t2 - t1,
+                                             "assembly_s": t3 - t2, "pack_s": t4 - t3}
+    return M, t4 - t0
 
 
 class _KPlus:
@@ -378,10 +384,13 @@ class FETISolver:
         return d_t, e_t
 
     def _sparse(self, r, c, v):
+        """The dual-space sparse operators (scaling W, fixed-dof correction C,
+        lumped preconditioner) in CSR: one sparse matrix-vector product each."""
         t = self.torch
         idx = t.from_numpy(np.vstack([r, c]).astype(np.int64))
-        return t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd),
-                                   check_invariants=True).coalesce().to(self.dev)
+        coo = t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd),
+                                  check_invariants=True).coalesce()
+        return coo.to_sparse_csr().to(self.dev)
 
     def _apply(self, M, x, out):
         """out = M x for a tile-packed operator of the plan's layout: the
