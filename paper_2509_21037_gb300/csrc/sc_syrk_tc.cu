@@ -76,15 +76,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 32, M = 128
+// K-major, N = 32 (idesc_n sets other N), M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tc(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tc(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// the instruction descriptor for N columns (M = 128)
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(n >> 3) << 17);
 }
 
 // bounded wait for the completion of phase `parity` of an mbarrier
@@ -168,8 +173,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int j = (isA ? j1lo : j2lo) + c - sn.jlo;
       const bool in = j >= 0 && j < sn.jhi - sn.jlo;
       const __nv_bfloat16 *src = in ? Yd + (int64_t)d * yd_plane + sn.yd_off + (int64_t)j * npad + k0 + 8 * kc : Yd;
+      // B: per K-slab the S planes one after the other (plane d = rows 32 d .. 32 d + 31 of an
+      // S * 32-row operand), so that planes 0 .. S - 1 - t form one K-major operand of
+      // 32 (S - t) rows for the MMA of A's plane t
       const uint32_t dst = base + (isA ? (uint32_t)d * kAPlane + tc_off(c, 8 * kc, kTileM)
-                                       : (uint32_t)S * kAPlane + (uint32_t)d * kBPlane + tc_off(c, 8 * kc, kTileN));
+                                       : (uint32_t)S * kAPlane + tc_off(32 * d + c, 8 * kc, 32 * S));
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
                    : "memory");
     }
@@ -254,17 +262,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;\n");
       const uint32_t st = smem0 + (uint32_t)(nb % kStages) * kStageBytes;
       const uint32_t dbuf = tmem + (uint32_t)(nb & 1) * kBufCols;
+      // For A's plane t, one MMA covers every B plane t' < S - t at once: N = 32 (S - t) and the
+      // output columns 32 (t + t') of group t + t', i.e. TMEM columns 32 t .. 32 S: 2 S MMAs per block
 #pragma unroll
-      for (int d = 0; d < S; ++d) {
+      for (int ta = 0; ta < S; ++ta) {
 #pragma unroll
-        for (int ta = 0; ta <= d; ++ta) {
-          const int tb = d - ta;
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t da = smem_desc(st + (uint32_t)ta * kAPlane + (uint32_t)ks * (kTileM * 32));
-            const uint64_t db = smem_desc(st + (uint32_t)S * kAPlane + (uint32_t)tb * kBPlane + (uint32_t)ks * (kTileN * 32));
-            mma_tc(dbuf + 32u * d, da, db, (ta > 0 || ks > 0) ? 1u : 0u);
-          }
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t da = smem_desc(st + (uint32_t)ta * kAPlane + (uint32_t)ks * (kTileM * 32));
+          const uint64_t db = smem_desc(st + (uint32_t)S * kAPlane + (uint32_t)ks * (kTileN * S * 32));
+          mma_tc(dbuf + 32u * ta, da, db, idesc_n(kTileN * (S - ta)), (ta > 0 || ks > 0) ? 1u : 0u);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(

@@ -264,7 +264,7 @@ class FETIResult:
     residuals: List[float]          # ||w_k|| / ||w_0|| per iteration
     continuity: float               # ||sum_i B_i u_i|| / max_i ||u_i||
     equilibrium: float              # max_i ||K_i u_i - f_i + B_i^T lambda|| / ||f_i||
-    apply_ms: float                 # mean device time of one F application (sc_apply + correction)
+    apply_ms: float                 # mean device time of one F application (one library apply)
     solve_ms: float                 # device time of the PCPG loop
 
 
@@ -282,7 +282,7 @@ class FETISolver:
 
     def __init__(self, problem, factored: Optional[Sequence] = None, device="cuda", precond: str = "lumped",
                  plan_kwargs: Optional[dict] = None, scaling: str = "bbt", dirichlet_setup: str = "auto",
-                 apply: str = "auto", check_every: int = 4):
+                 apply: str = "auto", check_every: int = 4, graph: bool = True):
         import torch
         if precond not in ("lumped", "dirichlet", "none"):
             raise ValueError(f"unknown preconditioner {precond!r}")
@@ -296,6 +296,8 @@ class FETISolver:
         self.apply_mode = ("mixed" if self.dev.type == "cuda" else "fp64") if apply == "auto" else apply
         self.apply_fp64_quarters = 1
         self.check_every = max(1, int(check_every))
+        self.use_graph = bool(graph)
+        self._st, self._graph = None, None
         subs = problem.subdomains
         self.subs = subs
         self.nd = int(problem.n_dual)
@@ -303,26 +305,27 @@ class FETISolver:
         self.plan, self.F = self._make_operator(plan_kwargs or {})
         self.R = [kernel_basis(sd) for sd in subs]
         self.kplus = [_KPlus(sd, f) for sd, f in zip(subs, self.fs)]
-        # G = [B_i R_i] and the two sparse dual operators: the fixed-dof
-        # correction C = sum_i B_i E_f B_i^T and the lumped preconditioner
-        gcols, crow, ccol, cval = [], [], [], []
+        # G = [B_i R_i]; the fixed-dof correction C_i = B_i E_f B_i^T (reading
+        # R17: F_i holds K_reg^-1 = K^+ + E_f) is subtracted from the stored
+        # F_i once, so that every application is one library call; the lumped
+        # preconditioner sum_i B_i K_i B_i^T
+        gcols = []
         M = sp.csr_matrix((self.nd, self.nd))
-        for sd, R in zip(subs, self.R):
+        for i, (sd, R) in enumerate(zip(subs, self.R)):
             Bt = sp.csc_matrix(sd.Bt)
             lm = np.asarray(sd.lambda_map, np.int64)
             BR = np.zeros((self.nd, R.shape[1]))
             np.add.at(BR, lm, Bt.T @ R)
             gcols.append(BR)
             Ef = sp.csr_matrix((np.ones(len(sd.fixed)), (sd.fixed, sd.fixed)), shape=Bt.shape[:1] * 2)
-            Cl = (Bt.T @ Ef @ Bt).tocoo()
-            crow.append(lm[Cl.row]); ccol.append(lm[Cl.col]); cval.append(Cl.data)
+            Cl = sp.tril(Bt.T @ Ef @ Bt).tocoo()
+            self.plan.add_symmetric(self.F, i, Cl.row, Cl.col, -Cl.data)
             if precond == "lumped":
                 Ml = (Bt.T @ sp.csr_matrix(sd.K) @ Bt).tocoo()
                 M = M + sp.csr_matrix((Ml.data, (lm[Ml.row], lm[Ml.col])), shape=(self.nd, self.nd))
         G = np.hstack(gcols)
         self.G = torch.from_numpy(G).to(self.dev)
         self.GtG_pinv = torch.from_numpy(np.linalg.pinv(G.T @ G, rcond=1e-12, hermitian=True)).to(self.dev)
-        self.C = self._sparse(np.concatenate(crow), np.concatenate(ccol), np.concatenate(cval))
         self.M = self._sparse(*_coo(M)) if precond == "lumped" else None
         self.q = torch.empty(self.nd, dtype=torch.float64, device=self.dev)
         self.Mdir, self.precond_setup_s = None, 0.0
@@ -384,27 +387,46 @@ class FETISolver:
         return d_t, e_t
 
     def _sparse(self, r, c, v):
-        """The dual-space sparse operators (scaling W, fixed-dof correction C,
-        lumped preconditioner) in CSR: one sparse matrix-vector product each."""
+        """A dual-space sparse operator (scaling W, lumped preconditioner) in
+        ELL form: per row the column indices and values padded to the longest
+        row (value 0, column of the row itself).  A product is one gather, one
+        multiply and one row sum, all on static index tensors (a CUDA graph
+        replays them)."""
         t = self.torch
-        idx = t.from_numpy(np.vstack([r, c]).astype(np.int64))
-        coo = t.sparse_coo_tensor(idx, t.from_numpy(np.asarray(v, np.float64)), (self.nd, self.nd),
-                                  check_invariants=True).coalesce()
-        return coo.to_sparse_csr().to(self.dev)
+        M = sp.csr_matrix((np.asarray(v, np.float64), (np.asarray(r, np.int64), np.asarray(c, np.int64))),
+                          shape=(self.nd, self.nd))
+        M.sum_duplicates()
+        cnt = np.diff(M.indptr)
+        width = max(1, int(cnt.max(initial=0)))
+        rows = np.repeat(np.arange(self.nd), cnt)
+        pos = np.arange(M.nnz) - np.repeat(M.indptr[:-1], cnt)
+        cols = np.repeat(np.arange(self.nd, dtype=np.int64)[:, None], width, axis=1)
+        vals = np.zeros((self.nd, width))
+        cols[rows, pos] = M.indices
+        vals[rows, pos] = M.data
+        return t.from_numpy(cols).to(self.dev), t.from_numpy(vals).to(self.dev)
+
+    @staticmethod
+    def _spmv(E, x):
+        cols, vals = E
+        return (vals * x[cols]).sum(dim=1)
 
     def _apply(self, M, x, out):
         """out = M x for a tile-packed operator of the plan's layout: the
         library's FP64 apply, or (apply="mixed") the tiles split between the
-        FP64 pipe and the integer pipes (sc_apply_mixed, same error bound)."""
+        FP64 pipe and the integer pipes (sc_apply_mixed, same error bound).
+        Launched on the current stream (the capture stream inside a graph)."""
+        stream = self.torch.cuda.current_stream(self.dev) if self.dev.type == "cuda" else None
         if self.apply_mode == "mixed":
-            self.plan.apply_mixed(M, x, out, self.apply_fp64_quarters)
+            self.plan.apply_mixed(M, x, out, self.apply_fp64_quarters, stream=stream)
         else:
-            self.plan.apply(M, x, out)
+            self.plan.apply(M, x, out, stream=stream)
 
     def apply_F(self, x):
-        """q = F x (library apply, then the fixed-dof correction)."""
+        """q = F x with F = sum_i B_i K_i^+ B_i^T (the stored F_i corrected
+        once for the fixed dofs): one library apply."""
         self._apply(self.F, x, self.q)
-        return self.q - self.torch.sparse.mm(self.C, x[:, None])[:, 0]
+        return self.q
 
     def project(self, x):
         return x - self.G @ (self.GtG_pinv @ (self.G.T @ x))
@@ -415,15 +437,65 @@ class FETISolver:
         t = self.torch
         if self.M is None and self.Mdir is None:
             return w
-        x = w if self.W is None else t.sparse.mm(self.W, w[:, None])[:, 0]
+        x = w if self.W is None else self._spmv(self.W, w)
         if self.M is not None:
-            y = t.sparse.mm(self.M, x[:, None])[:, 0]
+            y = self._spmv(self.M, x)
         else:
             self._apply(self.Mdir, x.contiguous(), self.qz)
             y = self.qz
         if self.W is not None:
-            y = t.sparse.mm(self.W, y[:, None])[:, 0]
+            y = self._spmv(self.W, y)
         return self.project(y)
+
+    def _state(self):
+        """The loop's device state: lambda, r, w, p, (z, w) of the previous
+        iteration and the residual norms of one chunk of check_every
+        iterations (static tensors: a CUDA graph of a chunk reads and writes
+        these)."""
+        if self._st is None:
+            t = self.torch
+            z = lambda: t.zeros(self.nd, dtype=t.float64, device=self.dev)
+            self._st = {"lam": z(), "r": z(), "w": z(), "p": z(),
+                        "zw_old": t.ones((), dtype=t.float64, device=self.dev),
+                        "norms": t.zeros(self.check_every, dtype=t.float64, device=self.dev)}
+        return self._st
+
+    def _step(self, st, k: int):
+        """One PCPG iteration on the state, in place; ||w|| goes to norms[k].
+        With p = 0 and (z, w)_old = 1 it is the first iteration (p = z)."""
+        t = self.torch
+        z = self.precondition(st["w"])
+        zw = t.dot(z, st["w"])
+        st["p"].mul_(zw / st["zw_old"]).add_(z)
+        qv = self.apply_F(st["p"])
+        eta = zw / t.dot(st["p"], qv)
+        st["lam"].add_(eta * st["p"])
+        st["r"].sub_(eta * qv)
+        st["w"].copy_(self.project(st["r"]))
+        st["zw_old"].copy_(zw)
+        st["norms"][k].copy_(t.linalg.vector_norm(st["w"]))
+
+    def _chunk_graph(self):
+        """A CUDA graph of check_every iterations (captured once: one step
+        run eagerly on finite data first, as capture wants, then the state is
+        left for solve() to reset).  None off CUDA or with graphs disabled."""
+        if not self.use_graph or self.dev.type != "cuda":
+            return None
+        if self._graph is None:
+            t = self.torch
+            st = self._state()
+            st["w"].fill_(1.0); st["r"].fill_(1.0); st["p"].zero_(); st["zw_old"].fill_(1.0)
+            side = t.cuda.Stream(self.dev)
+            side.wait_stream(t.cuda.current_stream(self.dev))
+            with t.cuda.stream(side):
+                self._step(st, 0)
+            t.cuda.current_stream(self.dev).wait_stream(side)
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g):
+                for k in range(self.check_every):
+                    self._step(st, k)
+            self._graph = g
+        return self._graph
 
     def solve(self, loads: Sequence[np.ndarray], tol: float = 1e-10, maxit: int = 1000,
               recover: bool = True) -> FETIResult:
@@ -435,40 +507,39 @@ class FETISolver:
         t = self.torch
         subs, nd = self.subs, self.nd
         d_t, e_t = self._rhs(loads)
+        graph = self._chunk_graph()
+        st = self._state()
         ev0, ev1 = self._events()
         ev0.record()
-        lam = self.G @ (self.GtG_pinv @ e_t)
-        r = d_t - self.apply_F(lam)
-        w = self.project(r)
-        w0 = t.linalg.vector_norm(w).item()
-        res, p, zw_old, it = [1.0], None, None, 0
+        st["lam"].copy_(self.G @ (self.GtG_pinv @ e_t))
+        st["r"].copy_(d_t - self.apply_F(st["lam"]))
+        st["w"].copy_(self.project(st["r"]))
+        st["p"].zero_()
+        st["zw_old"].fill_(1.0)
+        w0 = t.linalg.vector_norm(st["w"]).item()
+        res, it = [1.0], 0
         if w0 > 0:
             # the scalars stay on the device; the host reads the residual norms
-            # every check_every iterations (one synchronisation instead of one
-            # per iteration), so the GPU runs ahead of the loop in between
-            pending = []
-            for it in range(1, maxit + 1):
-                z = self.precondition(w)
-                zw = t.dot(z, w)
-                p = z if p is None else z + (zw / zw_old) * p
-                qv = self.apply_F(p)
-                eta = zw / t.dot(p, qv)
-                lam = lam + eta * p
-                r = r - eta * qv
-                w = self.project(r)
-                zw_old = zw
-                pending.append(t.linalg.vector_norm(w))
-                if it % self.check_every == 0 or it == maxit:
-                    vals = t.stack(pending).cpu().numpy() / w0
-                    pending = []
-                    hit = np.nonzero(vals < tol)[0]
-                    if len(hit):
-                        # the first iterate below tol is where the per-iteration loop would have stopped;
-                        # the few extra iterations only refine lambda further
-                        res.extend(vals[:hit[0] + 1].tolist())
-                        it = int(it - (len(vals) - 1 - hit[0]))
-                        break
-                    res.extend(vals.tolist())
+            # once per chunk of check_every iterations (one CUDA graph launch
+            # per full chunk), so the GPU runs the chunk without host gaps
+            while it < maxit:
+                n = min(self.check_every, maxit - it)
+                if graph is not None and n == self.check_every:
+                    graph.replay()
+                else:
+                    for k in range(n):
+                        self._step(st, k)
+                vals = st["norms"][:n].cpu().numpy() / w0
+                hit = np.nonzero(vals < tol)[0]
+                if len(hit):
+                    # the first iterate below tol is where the per-iteration loop would have stopped;
+                    # the few extra iterations only refine lambda further
+                    res.extend(vals[:hit[0] + 1].tolist())
+                    it += int(hit[0]) + 1
+                    break
+                res.extend(vals.tolist())
+                it += n
+        lam = st["lam"]
         ev1.record()
         ev1.synchronize()
         solve_ms = ev0.elapsed_time(ev1)

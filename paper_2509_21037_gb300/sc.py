@@ -175,6 +175,27 @@ class Plan:
             buf[off:off + tiles.numel()] = tiles
         return buf
 
+    def add_symmetric(self, F, i: int, rows, cols, vals):
+        """F_i[r, c] += v and F_i[c, r] += v (once for r == c) for entries
+        with r >= c, in place in the tile-packed layout (the lower tile holds
+        an off-diagonal-tile pair once; a diagonal tile stores both entries)."""
+        import torch
+        r = np.asarray(rows, np.int64)
+        c = np.asarray(cols, np.int64)
+        v = np.asarray(vals, np.float64)
+        assert np.all(r >= c) and len(r) == len(c) == len(v)
+        if len(r) == 0:
+            return
+        I, J = r // 32, c // 32
+        base = int(self.F_offsets[i]) + (I * (I + 1) // 2 + J) * 1024
+        off = [base + r % 32 + 32 * (c % 32)]
+        val = [v]
+        mirror = (I == J) & (r != c)                 # a diagonal tile holds the mirror entry too
+        off.append(base[mirror] + c[mirror] % 32 + 32 * (r[mirror] % 32))
+        val.append(v[mirror])
+        idx = torch.from_numpy(np.concatenate(off)).to(F.device)
+        F.index_add_(0, idx, torch.from_numpy(np.concatenate(val)).to(F.device))
+
     def enable_stage_timing(self, on: bool = True):
         self._check(self.lib.sc_enable_stage_timing(self.h, int(on)))
 

@@ -117,18 +117,26 @@ def tc_off(r: int, k: int, R: int) -> int:
     return (k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2
 
 
-def check_tile_fetches(T: dict, t, yd_plane: int) -> None:
+def check_tile_fetches(T: dict, t, yd_plane: int, S: int = 7) -> None:
     """The tcgen05 SYRK's 16-byte copies for one tile task: every source is
     inside its supernode's digit block of one plane (16-byte aligned), every
-    destination inside the stage and the stage's A and B parts covered once."""
+    destination inside the stage and the stage's A and B parts covered once
+    (A plane by plane, B slab-major: plane d is rows 32 d .. of an S * 32-row
+    operand, so that planes 0 .. S - 1 - t form the N = 32 (S - t) operand of
+    A's plane t)."""
     sns = T["sns"]
     lst = T["syrk_list"][t["list_off"]:t["list_off"] + t["list_len"]]
     j1lo, j2lo = int(t["q1"]) * 32, int(t["q2"]) * 32
     j1min = max(j1lo, j2lo)
     seen_a = set(tc_off(c, 8 * kc, 128) for c in range(128) for kc in range(4))
-    seen_b = set(tc_off(c, 8 * kc, 32) for c in range(32) for kc in range(4))
+    seen_b = set(tc_off(32 * d + c, 8 * kc, 32 * S) for d in range(S) for c in range(32) for kc in range(4))
     assert len(seen_a) == 512 and max(seen_a) + 16 <= 128 * 64 and all(o % 16 == 0 for o in seen_a)
-    assert len(seen_b) == 128 and max(seen_b) + 16 <= 32 * 64
+    assert len(seen_b) == 128 * S and max(seen_b) + 16 <= S * 32 * 64 and all(o % 16 == 0 for o in seen_b)
+    for ta in range(S):          # the MMA of A's plane ta reads B rows 0 .. 32 (S - ta) of each K-slab
+        for ks in range(2):
+            lo = ks * 32 * S * 32
+            rows = [tc_off(r, 16 * ks + k, 32 * S) for r in range(32 * (S - ta)) for k in range(16)]
+            assert min(rows) >= lo and max(rows) + 2 <= lo + 32 * S * 32
     for si in lst:
         s = sns[si]
         ns, ws = int(s["ns"]), int(s["jhi"] - s["jlo"])

@@ -190,7 +190,7 @@ def test_tile_plan_emulation_matches_oracle(name, prob):
                                                                   for i, v in enumerate(var)])
     for t in T["syrk"]:
         if int(t["sub"]) in tile_subs:
-            pe.check_tile_fetches(T, t, lay["yd_plane"])
+            pe.check_tile_fetches(T, t, lay["yd_plane"], var[int(t["sub"])])
     F = pe.emulate_assembly(T, plan.sizes, plan.stats, sc.concat_L_values(fs), tile_subs)
     assert not np.isnan(F).any(), "F entries left unwritten"
     Fo = oracle.dual_operators(prob.subdomains)

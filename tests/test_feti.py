@@ -206,7 +206,7 @@ class _DenseFETI(feti.FETISolver):
         subs = self.subs
 
         class _Plan:
-            def apply(self, F, x, q):
+            def apply(self, F, x, q, stream=None):
                 q.copy_(F @ x)
 
             def pack(self, blocks, device):
@@ -215,6 +215,13 @@ class _DenseFETI(feti.FETISolver):
                     lm = np.asarray(sd.lambda_map)
                     M[np.ix_(lm, lm)] += Bk
                 return torch.from_numpy(M)
+
+            def add_symmetric(self, F, i, rows, cols, vals):
+                lm = np.asarray(subs[i].lambda_map)
+                for r, c, v in zip(rows, cols, vals):
+                    F[lm[r], lm[c]] += v
+                    if r != c:
+                        F[lm[c], lm[r]] += v
 
         return _Plan(), torch.from_numpy(Fd)
 

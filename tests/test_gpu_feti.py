@@ -79,3 +79,23 @@ def test_dirichlet_setup_on_the_gpu_matches_host(name, dev):
         loads = feti.compatible_loads(prob, seed=2)
         ra, rb = gpu.solve(loads, tol=1e-10, recover=False), cpu.solve(loads, tol=1e-10, recover=False)
         assert abs(ra.iterations - rb.iterations) <= 1, (ra.iterations, rb.iterations)
+
+
+def test_graph_chunks_match_the_eager_loop(dev):
+    """The loop replayed as CUDA graphs of check_every iterations gives the
+    iterations and multipliers of the same steps launched one by one (the
+    mixed apply's atomics may order sums differently: 1e-10), and a maxit
+    that is no multiple of the chunk length runs the tail eagerly."""
+    prob = synth.make_config(2)
+    loads = feti.compatible_loads(prob, seed=1)
+    g = feti.FETISolver(prob, device=dev, precond="dirichlet")
+    e = feti.FETISolver(prob, g.fs, device=dev, precond="dirichlet", graph=False)
+    rg = g.solve(loads, tol=1e-10, recover=False)
+    re = e.solve(loads, tol=1e-10, recover=False)
+    assert g._graph is not None and e._graph is None
+    assert abs(rg.iterations - re.iterations) <= 1, (rg.iterations, re.iterations)
+    assert np.linalg.norm(rg.lam - re.lam) <= 1e-10 * np.linalg.norm(re.lam)
+    print(f"config 2 Dirichlet: graph {rg.solve_ms / rg.iterations:.3f} ms/iteration, "
+          f"eager {re.solve_ms / re.iterations:.3f} ms/iteration ({rg.iterations} iterations)")
+    short = g.solve(loads, tol=1e-30, maxit=2 * g.check_every + 1, recover=False)
+    assert short.iterations == 2 * g.check_every + 1 and len(short.residuals) == short.iterations + 1
