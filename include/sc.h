@@ -285,6 +285,42 @@ sc_status sc_apply_fixed(sc_ctx *ctx, const double *F_dev, const double *lambda_
 sc_status sc_apply_mixed(sc_ctx *ctx, const double *F_dev, const double *lambda_dev, double *q_dev,
                          int32_t fp64_quarters, void *stream);
 
+/* ---- the product from a digit form of F, on the tensor cores ----------------
+ * (paper Eq. "dualop_apply_expl"; the digit form and its tensor-core product
+ * are this library's.)  sc_apply_digits_prepare writes, once per assembly, a
+ * digit form of the tile-packed F: every stored 32x32 tile in 55-bit fixed
+ * point against its largest exponent, as seven balanced base-256 digits of
+ * one byte each (7184 bytes per tile against 8192 in FP64).  sc_apply_digits
+ * then forms q = F lambda from it with exact integer digit products on the
+ * FP16 tensor cores (mma.sync) and one FP64 scaling per row and tile: the
+ * error is that of holding each tile and 32-entry block of lambda in 55 bits
+ * against their largest entries (below 2^-49 of 32 max|tile| max|block| per
+ * row and tile), the size of an FP64 product's rounding. */
+
+/* Bytes of the digit-form buffer Fd: the digit tiles, per-call scratch for
+ * the digits of lambda (944 bytes per 32-row block of every F_i) and a
+ * 16-byte status word. */
+sc_status sc_apply_digits_size(const sc_ctx *ctx, int64_t *bytes);
+
+/* Fd_dev (device, sc_apply_digits_size bytes, 16-byte aligned, caller-owned)
+ * := the digit form of F_dev (tile-packed, as written by sc_assemble_batch or
+ * any operator of the same layout, every entry finite).  Asynchronous on
+ * `stream`; F_dev is only read. */
+sc_status sc_apply_digits_prepare(sc_ctx *ctx, const double *F_dev, void *Fd_dev, void *stream);
+
+/* q_dev (n_dual doubles, overwritten) := sum_i scatter_i(F_i gather_i(lambda))
+ * from the digit form Fd_dev (sc_apply_digits_prepare).  The call writes the
+ * scratch part of Fd_dev: calls on one Fd_dev must not overlap.  Asynchronous
+ * on `stream`; SC_ERR_STATE if the plan has no lambda_map.  The kernel's
+ * waits for its bulk copies are bounded by sc_options.poll_limit polls; one
+ * that gives up sets the timeout bit of Fd_dev's status word (q is then
+ * incomplete). */
+sc_status sc_apply_digits(sc_ctx *ctx, void *Fd_dev, const double *lambda_dev, double *q_dev, void *stream);
+
+/* Reads and clears Fd_dev's status word (synchronises `stream`): SC_OK, or
+ * SC_ERR_TIMEOUT if a call since the last check gave up a bounded wait. */
+sc_status sc_apply_digits_status(sc_ctx *ctx, void *Fd_dev, void *stream);
+
 /* Expand F_i into a dense full m_i x m_i column-major device matrix dst_dev
  * with leading dimension ld >= m_i.  Asynchronous on `stream`. */
 sc_status sc_export_F(sc_ctx *ctx, const double *F_dev, int32_t i, double *dst_dev, int32_t ld,

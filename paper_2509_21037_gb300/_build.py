@@ -59,7 +59,8 @@ def build(verbose: bool = False, extra_nvcc: List[str] = ()) -> str:
     os.makedirs(OBJ, exist_ok=True)
     cuda = _cuda_home()
     cu_main = ["sc_plan.cpp", "sc_api.cu", "sc_kernels.cu", "sc_static.cu", "sc_split.cu", "sc_mlp.cu",
-               "sc_implicit.cu", "sc_apply_fixed.cu", "sc_probe.cu", "sc_syrk_tc.cu", "sc_select.cu"]
+               "sc_implicit.cu", "sc_apply_fixed.cu", "sc_probe.cu", "sc_syrk_tc.cu", "sc_select.cu",
+               "sc_apply_digits.cu"]
     objs_main = []
     cmds = []
     for s in cu_main:

@@ -67,6 +67,10 @@ SC_SYMBOLS = {
     "sc_apply": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply_fixed": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
     "sc_apply_mixed": ([c_vp, c_vp, c_vp, c_vp, c_i32, c_vp], c_int),
+    "sc_apply_digits_size": ([c_vp, ctypes.POINTER(ctypes.c_int64)], c_int),
+    "sc_apply_digits_prepare": ([c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_apply_digits": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_int),
+    "sc_apply_digits_status": ([c_vp, c_vp, c_vp], c_int),
     "sc_export_F": ([c_vp, c_vp, c_i32, c_vp, c_i32, c_vp], c_int),
     "sc_enable_stage_timing": ([c_vp, c_i32], c_int),
     "sc_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), c_i32], c_int),

@@ -290,10 +290,12 @@ class FETISolver:
             raise ValueError(f"unknown scaling {scaling!r}")
         self.torch = torch
         self.dev = torch.device(device)
-        if apply not in ("auto", "fp64", "mixed"):
+        if apply not in ("auto", "fp64", "mixed", "digits"):
             raise ValueError(f"unknown apply {apply!r}")
-        # the operator applies: "mixed" (sc_apply_mixed) on a CUDA device by default
-        self.apply_mode = ("mixed" if self.dev.type == "cuda" else "fp64") if apply == "auto" else apply
+        # the operator applies: on a CUDA device by default "digits" (sc_apply_digits: the
+        # operators' digit forms, prepared once at set-up, on the tensor cores)
+        self.apply_mode = ("digits" if self.dev.type == "cuda" else "fp64") if apply == "auto" else apply
+        self._digit_forms = {}
         self.apply_fp64_quarters = 1
         self.check_every = max(1, int(check_every))
         self.use_graph = bool(graph)
@@ -352,6 +354,11 @@ class FETISolver:
         self.W = None
         if precond != "none" and scaling == "bbt":
             self.W = self._sparse(*_coo(bbt_inverse(subs, self.nd)))
+        if self.apply_mode == "digits":
+            # after the fixed-dof correction: the digit forms are of the final operators
+            for M in (self.F, self.Mdir):
+                if M is not None:
+                    self._digit_forms[M.data_ptr()] = self.plan.prepare_digits(M)
 
     def _make_operator(self, plan_kwargs: dict):
         """The library's plan and assembled F (tile-packed, on the device)."""
@@ -413,11 +420,15 @@ class FETISolver:
 
     def _apply(self, M, x, out):
         """out = M x for a tile-packed operator of the plan's layout: the
-        library's FP64 apply, or (apply="mixed") the tiles split between the
-        FP64 pipe and the integer pipes (sc_apply_mixed, same error bound).
-        Launched on the current stream (the capture stream inside a graph)."""
+        library's FP64 apply; (apply="mixed") the tiles split between the FP64
+        pipe and the integer pipes (sc_apply_mixed); or (apply="digits") the
+        operator's digit form on the tensor cores (sc_apply_digits); all three
+        round at the FP64 level.  Launched on the current stream (the capture
+        stream inside a graph)."""
         stream = self.torch.cuda.current_stream(self.dev) if self.dev.type == "cuda" else None
-        if self.apply_mode == "mixed":
+        if self.apply_mode == "digits":
+            self.plan.apply_digits(self._digit_forms[M.data_ptr()], x, out, stream=stream)
+        elif self.apply_mode == "mixed":
             self.plan.apply_mixed(M, x, out, self.apply_fp64_quarters, stream=stream)
         else:
             self.plan.apply(M, x, out, stream=stream)

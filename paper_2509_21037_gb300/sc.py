@@ -141,6 +141,34 @@ class Plan:
         self._check(self.lib.sc_apply_mixed(self.h, F.data_ptr(), lam.data_ptr(), q.data_ptr(), int(fp64_quarters),
                                             _stream_ptr(stream)))
 
+    def digits_size(self) -> int:
+        """Bytes of the digit form of F (include/sc.h, sc_apply_digits_size)."""
+        import ctypes
+        n = ctypes.c_int64(0)
+        self._check(self.lib.sc_apply_digits_size(self.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def prepare_digits(self, F, Fd=None, stream=None):
+        """The digit form of a tile-packed operator F for apply_digits
+        (sc_apply_digits_prepare); allocated here when Fd is None."""
+        import torch
+        if Fd is None:
+            Fd = torch.empty(max(16, self.digits_size()), dtype=torch.uint8, device=F.device)
+        self._check(self.lib.sc_apply_digits_prepare(self.h, F.data_ptr(), Fd.data_ptr(), _stream_ptr(stream)))
+        return Fd
+
+    def apply_digits(self, Fd, lam, q, stream=None):
+        """q = F * lambda on the tensor cores from the digit form
+        (include/sc.h, sc_apply_digits)."""
+        self._check(self.lib.sc_apply_digits(self.h, Fd.data_ptr(), lam.data_ptr(), q.data_ptr(),
+                                             _stream_ptr(stream)))
+
+    def digits_status(self, Fd, stream=None) -> int:
+        """Status of the apply_digits calls on Fd since the last check
+        (sc_apply_digits_status: synchronises the stream, resets the word):
+        abi.SC_OK or abi.SC_ERR_TIMEOUT."""
+        return self.lib.sc_apply_digits_status(self.h, Fd.data_ptr(), _stream_ptr(stream))
+
     def export(self, F, i: int, dst=None, stream=None):
         import torch
         m = self.m[i]
