@@ -771,6 +771,92 @@ def _split_section(args, fs, prob, Lv, lam, flush, stream, dev, fp64_ms):
     return out
 
 
+def _apply_suite(plan, F, lam, q, steps):
+    """Every form of the explicit product on one assembled F: the FP64 apply,
+    the integer-pipe fixed point and the tensor-core digit form (prepared
+    once), each timed back to back over `steps` calls (F is larger than L2);
+    bytes are the stored triangle in FP64 (fp64, fixed) or the streamed digit
+    tiles (digits), against the measured HBM peak."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    by = plan.stats.bytes_apply
+
+    def time_it(fn):
+        fn()
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / steps
+
+    out = {}
+    t = time_it(lambda: plan.apply(F, lam, q))
+    out["fp64"] = {"ms": t, "GBps": by / (t / 1e3) / 1e9, "frac_hbm": by / (t / 1e3) / 1e9 / HBM_PEAK_GBPS}
+    qx = torch.empty_like(q)
+    t = time_it(lambda: plan.apply_fixed(F, lam, qx))
+    out["fixed"] = {"ms": t, "GBps": by / (t / 1e3) / 1e9, "frac_hbm": by / (t / 1e3) / 1e9 / HBM_PEAK_GBPS,
+                    "rel_diff_vs_fp64": (torch.linalg.vector_norm(qx - q) / torch.linalg.vector_norm(q)).item()}
+    Fd = plan.prepare_digits(F)
+    a.record()
+    plan.prepare_digits(F, Fd)
+    b.record()
+    b.synchronize()
+    t_prep = a.elapsed_time(b)
+    t = time_it(lambda: plan.apply_digits(Fd, lam, qx))
+    dby = plan.sizes.F_doubles // 1024 * 7184 + 16.0 * sum(plan.m)
+    out["digits"] = {"ms": t, "bytes": dby, "GBps": dby / (t / 1e3) / 1e9,
+                     "frac_hbm": dby / (t / 1e3) / 1e9 / HBM_PEAK_GBPS, "prepare_ms": t_prep,
+                     "speedup_vs_fp64": out["fp64"]["ms"] / t,
+                     "rel_diff_vs_fp64": (torch.linalg.vector_norm(qx - q) / torch.linalg.vector_norm(q)).item()}
+    if plan.digits_status(Fd) != 0:
+        raise RuntimeError("sc_apply_digits reported a timeout")
+    del Fd
+    out["bytes_fp64"] = by
+    out["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    return out
+
+
+def run_config3(args):
+    """512 elasticity cubes (edge 8..16), FP64 path: assembly and every form of
+    the explicit product (the apply roofline at a second size)."""
+    import torch
+
+    from paper_2509_21037_gb300 import host, sc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prob = synth.make_config(3, seed=args.seed)
+    fs = host.factorize_problem(prob.subdomains, threads=0)
+    Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
+    lam = torch.from_numpy(np.random.default_rng(args.seed).standard_normal(prob.n_dual)).to(dev)
+    plan = sc.Plan(fs, prob.n_dual).upload(dev)
+    F = plan.new_F(dev)
+    q = torch.empty_like(lam)
+    for _ in range(args.warmup):
+        plan.assemble(Lv, F)
+    torch.cuda.synchronize(dev)
+    if plan.device_status() != 0:
+        raise RuntimeError("device status not OK (config 3)")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(args.steps):
+        a.record()
+        plan.assemble(Lv, F)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    plan.apply(F, lam, q)
+    t = sum(ms) / len(ms)
+    line = {"metric": METRIC, "value": len(fs) / (t / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "elasticity3d_hex8_512_cubes_k8-16", "subdomains": len(fs),
+                       "multipliers_total": int(prob.n_dual), "seed": args.seed},
+            "sc_apply": _apply_suite(plan, F, lam, q, 20)}
+    print(json.dumps(line, default=_json_default))
+    return 0
+
+
 def run_config5(args):
     """Mixed batch: 1024 2D heat squares (edge 32..96) + 1024 3D elasticity cubes
     (edge 8..20), learned per-subdomain variant selection (autotuner on a third
@@ -817,18 +903,10 @@ def run_config5(args):
             c.synchronize()
             asm.append(a.elapsed_time(b))
             app.append(b.elapsed_time(c))
-        qf = torch.empty_like(lam)
-        b.record()
-        for _ in range(args.steps):
-            plan.apply_fixed(F, lam, qf)
-        c.record()
-        c.synchronize()
-        fx = b.elapsed_time(c) / args.steps
         out = {"assembly_ms": sum(asm) / len(asm), "apply_ms": sum(app) / len(app),
                "waves": int(plan.stats.n_waves), "ws_GB": plan.sizes.ws_bytes / 1e9,
                "apply_GBps": plan.stats.bytes_apply / (sum(app) / len(app) / 1e3) / 1e9,
-               "apply_fixed_ms": fx, "apply_fixed_GBps": plan.stats.bytes_apply / (fx / 1e3) / 1e9,
-               "apply_fixed_rel_diff": (torch.linalg.vector_norm(qf - q) / torch.linalg.vector_norm(q)).item()}
+               "sc_apply": _apply_suite(plan, F, lam, q, 20)}
         F_off = plan.F_offsets.copy()
         st = plan.stats_dict()
         out["q"] = q
@@ -903,8 +981,9 @@ def main():
                     help="skip the split-precision (tensor-core) variant of the workload")
     ap.add_argument("--split-slices", type=int, nargs="+", default=[7, 5])
     ap.add_argument("--no-split-error", dest="split_error", action="store_false")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 5],
-                    help="2: the 64-subdomain heat cube (default); 5: the mixed 2048-subdomain batch")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 5],
+                    help="2: the 64-subdomain heat cube (default); 3: 512 elasticity cubes (FP64 path and "
+                         "the product forms); 5: the mixed 2048-subdomain batch")
     ap.add_argument("--tol", type=float, default=1e-8, help="config 5: error target of the variant selection")
     ap.add_argument("--ws-limit-gb", type=float, default=48.0, help="config 5: workspace bound per wave")
     ap.add_argument("--profile-slices", type=int, default=0,
@@ -924,6 +1003,8 @@ def main():
         return run_reference(args)
     if args.config == 5:
         return run_config5(args)
+    if args.config == 3:
+        return run_config3(args)
     return run_sc(args)
 
 
