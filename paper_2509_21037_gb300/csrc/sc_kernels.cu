@@ -127,19 +127,26 @@ __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, c
       }
       __syncthreads();
       // Update of the rows below.  The FP64 pipe charges a warp instruction in
-      // full whatever the number of active lanes, so a column range narrower
-      // than 32 is packed: lane groups of W >= wk lanes (a power of two) take
-      // 32 / W rows per warp step.
-      const int W = wk <= 4 ? 4 : wk <= 8 ? 8 : wk <= 16 ? 16 : 32;
-      const int R = 32 / W, cl = lane & (W - 1), ro = lane / W;
-      if (cl < wk) {
-        for (int p = kb + kw + warp * R + ro; p < nrow; p += (kThreads / 32) * R) {
+      // full whatever the number of active lanes, so the (row, column) pairs
+      // of the update are numbered row-major over the wk live columns and
+      // dealt to the CTA's threads in turn: every lane of a warp step works
+      // (but the last), whatever wk is.
+      {
+        const int dp = kThreads / wk, dc = kThreads - dp * wk;   // one step of kThreads pairs
+        int p = kb + kw + tid / wk, cl = tid - (tid / wk) * wk;
+        while (p < nrow) {                                       // pair (p, cl) exists iff p < nrow
           // the target row is the accumulator: no separate subtraction on the FP64 pipe
           double *tg = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
           double acc = tg[cl];
 #pragma unroll 8
           for (int q = 0; q < kw; ++q) acc = fma(-Lv[cps[q] + p], Xs[q][cl], acc);
           tg[cl] = acc;
+          p += dp;
+          cl += dc;
+          if (cl >= wk) {
+            cl -= wk;
+            ++p;
+          }
         }
       }
       __syncthreads();
@@ -156,7 +163,7 @@ __device__ __forceinline__ int tri_warp(unsigned k) { return (int)((k * 26544357
 // Work-queue form (queue != nullptr): a grid sized to the resident CTAs pulls
 // task indices from an atomic counter until the list is exhausted; otherwise
 // one CTA per task.  Tasks are ordered largest first by the planner.
-__global__ void __launch_bounds__(kThreads) trsm_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+__global__ void __launch_bounds__(kThreads, 16) trsm_kernel(const PlanPtrs P, const double *__restrict__ Lv,
                                                         const double *__restrict__ invd, double *__restrict__ Y,
                                                         unsigned *queue, int ntask) {
   __shared__ double Xs[32][33];
