@@ -163,8 +163,13 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _kernel_source_hash():
-    src = os.path.join(ROOT, "paper_2509_21037_gb300", "csrc", "sc_kernels.cu")
+# the source file of each profiled kernel
+_KERNEL_SOURCE = {"apply_digits_kernel": "sc_apply_digits.cu", "apply_fixed_kernel": "sc_apply_fixed.cu",
+                  "implicit_kernel": "sc_implicit.cu"}
+
+
+def _kernel_source_hash(kernel: str = "syrk_kernel"):
+    src = os.path.join(ROOT, "paper_2509_21037_gb300", "csrc", _KERNEL_SOURCE.get(kernel, "sc_kernels.cu"))
     return hashlib.sha256(open(src, "rb").read()).hexdigest()
 
 
@@ -177,7 +182,7 @@ def _traffic_for(kernel: str):
     try:
         d = json.load(open(path))
         e = d.get(kernel)
-        if e and e.get("source_sha256") == _kernel_source_hash():
+        if e and e.get("source_sha256") == _kernel_source_hash(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -266,9 +271,19 @@ def _gpu_implicit(fs, n_dual, Lv, lam, q_expl, stream, reps=20):
     ms = a0.elapsed_time(a1) / reps
     tf = ip.sizes.flops / (ms / 1e3) / 1e12
     diff = (torch.linalg.vector_norm(q - q_expl) / torch.linalg.vector_norm(q_expl)).item()
+    # the same with one CTA per subdomain (no CTA pairs), for the comparison
+    one = implicit.ImplicitPlan(fs, n_dual, pairs=-1).upload(lam.device)
+    one.apply(Lv, lam, q, stream)
+    a0.record(stream)
+    for _ in range(reps):
+        one.apply(Lv, lam, q, stream)
+    a1.record(stream)
+    a1.synchronize()
+    ms_one = a0.elapsed_time(a1) / reps
+    del one
     return ms, {"ms": ms, "flops": ip.sizes.flops, "nnz_visited": int(ip.sizes.nnz_visited),
                 "max_levels": int(ip.sizes.max_levels), "tflops": tf, "frac_fp64_peak_nominal": tf / FP64_PEAK_TFLOPS,
-                "rel_diff_vs_explicit": diff}
+                "rel_diff_vs_explicit": diff, "ms_one_cta_per_subdomain": ms_one}
 
 
 def _fp64_fma_peak(dev, stream):
@@ -574,6 +589,7 @@ def run_sc(args):
         "frac_hbm": dig_bytes / (t_dig / 1e3) / 1e9 / HBM_PEAK_GBPS,
         "fp64_form_GBps": st["bytes_apply"] / (t_dig / 1e3) / 1e9,
         "speedup_vs_fp64": t_expl / t_dig, "prepare_ms": t_prep,
+        "traffic": _traffic_for("apply_digits_kernel"),
         "rel_diff_vs_fp64": (torch.linalg.vector_norm(qd - q) / torch.linalg.vector_norm(q)).item()}
     del Fd
     apply_sec = {

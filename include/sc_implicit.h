@@ -77,9 +77,18 @@ typedef struct {
  * subdomains; on a batch of similar subdomains they cost more (cluster
  * barriers, L1-bypassing reads of x) than they give.  0 puts every subdomain
  * on a cluster. */
+/* pairs: 1 solves each subdomain below cluster_min_work whose visited etree
+ * splits on a pair of CTAs: the subtrees below the first node with two or
+ * more substantial visited subtrees are dealt to the two CTAs (about half the
+ * work each), which solve them at the same time; the chain above runs on the
+ * first CTA; three cluster barriers per call.  0 (automatic) and -1: one CTA
+ * per subdomain (on GB300 the pair form measured slower on the 64-subdomain
+ * heat batch: the per-level chains, not the subtrees, bound the solve).
+ * reserved: 0. */
 typedef struct {
   int64_t cluster_min_work;
-  int32_t reserved[2];
+  int32_t pairs;
+  int32_t reserved;
 } sci_options;
 
 /* Symbolic stage (host only): validates the patterns (the rules of sc_plan)

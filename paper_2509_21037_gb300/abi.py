@@ -91,7 +91,7 @@ class ImplicitSizes(ctypes.Structure):
 
 
 class ImplicitOptions(ctypes.Structure):
-    _fields_ = [("cluster_min_work", c_i64), ("reserved", c_i32 * 2)]
+    _fields_ = [("cluster_min_work", c_i64), ("pairs", c_i32), ("reserved", c_i32)]
 
 
 # every symbol include/sc_implicit.h declares

@@ -65,9 +65,14 @@ struct ISub {
   int32_t lev_lo, n_lev;        // level boundaries levptr[lev_lo .. lev_lo + n_lev]
   int32_t g_lo, g_hi;           // gather rows
   int32_t s_lo, s_hi;           // scatter entries
+  // solved by a CTA pair (item kind 2): the levels are those of subtree part
+  // A (n_lev_a), then part B (n_lev_b), then the top chain above the split;
+  // scatter entries [s_lo, s_mid1) lie in part A, [s_mid1, s_mid2) in B, the
+  // rest in the top.  Otherwise n_lev_a = n_lev_b = 0, s_mid1 = s_mid2 = s_lo.
+  int32_t n_lev_a, n_lev_b, s_mid1, s_mid2;
   int32_t pad;
 };
-static_assert(sizeof(ISub) == 48, "ISub layout");
+static_assert(sizeof(ISub) == 64, "ISub layout");
 
 struct ISn {
   int64_t lval;      // absolute index of L(c0, c0) in the concatenated values
@@ -87,7 +92,8 @@ struct ISEnt {
 };
 
 struct IItem {
-  int32_t kind;                 // 0: sub[0] on the whole cluster; 1: sub[r] on CTA r, r < n
+  int32_t kind;                 // 0: sub[0] on the whole cluster; 1: sub[r] on CTA r, r < n;
+                                // 2: sub[j] on the CTA pair (2j, 2j + 1), j < n <= kCluster / 2
   int32_t n;
   int32_t sub[kCluster];        // indices into the subdomain table
 };
@@ -113,6 +119,7 @@ struct IPtrs {
   const IEnt *gent;
   const ISEnt *sent;
   const IItem *items;
+  int64_t rd_off;      // doubles from a subdomain's x to its reciprocal diagonals (workspace)
 };
 
 __device__ __forceinline__ int64_t col_off(int t, int nr) {
@@ -131,14 +138,9 @@ __device__ __forceinline__ double ldx(const double *p) {
 // written to x; returns the lane's y (0 for lanes >= w).
 template <bool CL>
 __device__ __forceinline__ double forward_triangle(const double *__restrict__ L, int nr, int kb, int w, double *xs,
-                                                   uint32_t *status, int lane) {
+                                                   int64_t rd_off, int lane) {
   const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
-  double inv = 0.0;
-  if (lane < w) {
-    const double d = L[coff];
-    if (d > 0.0 && d <= 1.79769313486231570e308) inv = 1.0 / d;
-    else atomicOr(status, 1u);
-  }
+  const double inv = lane < w ? ldx<CL>(xs + rd_off + kb + lane) : 0.0;   // 1 / L(c, c), computed per call
   // lane i: L(kb + i, kb + k) for k < i, entry (i - k) of column kb + k
   double lv[32];
 #pragma unroll
@@ -212,11 +214,35 @@ __device__ __forceinline__ double transpose_reduce(double (&acc)[32], int lane) 
   return acc[0];
 }
 
+// The same for the first w < 32 columns (acc[k] = 0 for k >= w): a
+// transpose-reduce over groups of P lanes (P the power of two >= w), then a
+// butterfly across the 32 / P groups: P - 1 + 5 - log2 P additions instead of 31.
+__device__ __forceinline__ double transpose_reduce_w(double (&acc)[32], int lane, int w) {
+  if (w > 16) return transpose_reduce(acc, lane);
+  const int P = w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : 16;
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    if (h < P) {   // uniform
+      const bool up = (lane & h) != 0;
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const double send = up ? acc[j] : acc[j + h];
+        const double keep = up ? acc[j + h] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(kFull, send, h);
+      }
+    }
+  }
+  double v = acc[0];
+  for (int m = P; m < 32; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
+  return v;
+}
+
 // Backward triangle of one block (one warp, lane = column): z = L_bb^{-T} rhs, written to x.
+template <bool CL>
 __device__ __forceinline__ void backward_triangle(const double *__restrict__ L, int nr, int kb, int w, double rhs,
-                                                  double *xs, int lane) {
+                                                  double *xs, int64_t rd_off, int lane) {
   const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
-  const double inv = lane < w ? 1.0 / L[coff] : 0.0;
+  const double inv = lane < w ? ldx<CL>(xs + rd_off + kb + lane) : 0.0;
   // lane k: L(kb + i, kb + k) for i > k, entry (i - k) of its own column
   double lc[32];
 #pragma unroll
@@ -232,38 +258,52 @@ __device__ __forceinline__ void backward_triangle(const double *__restrict__ L, 
   if (lane < w) xs[kb + lane] = rhs;
 }
 
-// A group of warps solving supernodes together: the whole cluster, or one
-// CTA.  Warps are numbered across the group.
+// A group of warps solving supernodes together: the whole cluster, one CTA,
+// or a subgroup of a CTA's warps (consecutive warps w0 .. w0 + nwl - 1 with
+// their own named barrier `bar`).  warp: the warp's index in its CTA; gw,
+// nw: its index and the warp count across the group; slot: the group's row
+// of the CTA's 32-double reduction buffer.
 struct Group {
   int rank, size, warp, lane, gw, nw;
   bool cluster;
+  int w0, nwl, bar, slot;
+  // the warps of the group in this CTA
+  __device__ void sync_cta() const {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "r"(32 * nwl) : "memory");
+  }
   __device__ void sync() const {
     if (cluster) cg::this_cluster().sync();
-    else __syncthreads();
+    else sync_cta();
   }
 };
 
 __device__ __forceinline__ Group cta_group(int warp, int lane) {
-  return Group{0, 1, warp, lane, warp, kWarps, false};
+  return Group{0, 1, warp, lane, warp, kWarps, false, 0, kWarps, 0, 0};
+}
+
+// warps [w0, w0 + nwl) of this CTA, named barrier 1 + slot (slot < kWarps - 1)
+__device__ __forceinline__ Group sub_group(int warp, int lane, int w0, int nwl, int slot) {
+  return Group{0, 1, warp, lane, warp - w0, nwl, false, w0, nwl, nwl == kWarps ? 0 : 1 + slot, slot};
 }
 
 __device__ __forceinline__ Group cluster_group(int warp, int lane) {
   cg::cluster_group c = cg::this_cluster();
   const int r = (int)c.block_rank(), n = (int)c.num_blocks();
-  return Group{r, n, warp, lane, r * kWarps + warp, n * kWarps, true};
+  return Group{r, n, warp, lane, r * kWarps + warp, n * kWarps, true, 0, kWarps, 0, 0};
 }
 
 // One supernode by one warp.
 template <bool CL>
 __device__ void forward_warp(const ISn &sn, const double *__restrict__ Lv, const int32_t *__restrict__ rows,
-                             double *x, double *ys, uint32_t *status, int lane) {
+                             double *x, double *ys, int64_t rd_off, int lane) {
   const int ns = sn.ns, nr = ns + sn.rs;
   const double *L = Lv + sn.lval;
   const int32_t *R = rows + sn.rows_off;
   double *xs = x + sn.c0;
   for (int kb = 0; kb < ns; kb += 32) {
     const int w = min(32, ns - kb);
-    ys[lane] = forward_triangle<CL>(L, nr, kb, w, xs, status, lane);
+    ys[lane] = forward_triangle<CL>(L, nr, kb, w, xs, rd_off, lane);
     __syncwarp();
     for (int t0 = kb + w; t0 < nr; t0 += 32) forward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, ys, xs, x, lane);
     __syncwarp();
@@ -272,7 +312,7 @@ __device__ void forward_warp(const ISn &sn, const double *__restrict__ Lv, const
 
 template <bool CL>
 __device__ void backward_warp(const ISn &sn, const double *__restrict__ Lv, const int32_t *__restrict__ rows,
-                              double *x, int lane) {
+                              double *x, int64_t rd_off, int lane) {
   const int ns = sn.ns, nr = ns + sn.rs;
   const double *L = Lv + sn.lval;
   const int32_t *R = rows + sn.rows_off;
@@ -283,9 +323,9 @@ __device__ void backward_warp(const ISn &sn, const double *__restrict__ Lv, cons
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0.0;
     for (int t0 = kb + w; t0 < nr; t0 += 32) backward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, xs, x, acc, lane);
-    const double part = transpose_reduce(acc, lane);
+    const double part = transpose_reduce_w(acc, lane, w);
     const double rhs = lane < w ? ldx<CL>(xs + kb + lane) - part : 0.0;
-    backward_triangle(L, nr, kb, w, rhs, xs, lane);
+    backward_triangle<CL>(L, nr, kb, w, rhs, xs, rd_off, lane);
     __syncwarp();
   }
 }
@@ -295,14 +335,14 @@ __device__ void backward_warp(const ISn &sn, const double *__restrict__ Lv, cons
 // spread over all the group's warps.
 template <bool CL>
 __device__ void forward_group(const Group &g, const ISn &sn, const double *__restrict__ Lv,
-                              const int32_t *__restrict__ rows, double *x, double *ys, uint32_t *status) {
+                              const int32_t *__restrict__ rows, double *x, double *ys, int64_t rd_off) {
   const int ns = sn.ns, nr = ns + sn.rs;
   const double *L = Lv + sn.lval;
   const int32_t *R = rows + sn.rows_off;
   double *xs = x + sn.c0;
   for (int kb = 0; kb < ns; kb += 32) {
     const int w = min(32, ns - kb);
-    if (g.gw == 0) forward_triangle<CL>(L, nr, kb, w, xs, status, g.lane);
+    if (g.gw == 0) forward_triangle<CL>(L, nr, kb, w, xs, rd_off, g.lane);
     g.sync();
     ys[g.lane] = g.lane < w ? ldx<CL>(xs + kb + g.lane) : 0.0;
     __syncwarp();
@@ -316,7 +356,8 @@ __device__ void forward_group(const Group &g, const ISn &sn, const double *__res
 // the group's first CTA through distributed shared memory when CL).
 template <bool CL>
 __device__ void backward_group(const Group &g, const ISn &sn, const double *__restrict__ Lv,
-                               const int32_t *__restrict__ rows, double *x, double *red, double *red_cta) {
+                               const int32_t *__restrict__ rows, double *x, int64_t rd_off, double *red,
+                               double *red_cta) {
   const int ns = sn.ns, nr = ns + sn.rs;
   const double *L = Lv + sn.lval;
   const int32_t *R = rows + sn.rows_off;
@@ -328,44 +369,148 @@ __device__ void backward_group(const Group &g, const ISn &sn, const double *__re
     for (int k = 0; k < 32; ++k) acc[k] = 0.0;
     for (int t0 = kb + w + 32 * g.gw; t0 < nr; t0 += 32 * g.nw)
       backward_panel_chunk<CL>(L, R, ns, nr, kb, w, t0, xs, x, acc, g.lane);
-    red[g.warp * 32 + g.lane] = transpose_reduce(acc, g.lane);
-    __syncthreads();
-    if (g.warp == 0) {
+    red[g.warp * 32 + g.lane] = transpose_reduce_w(acc, g.lane, w);
+    g.sync_cta();
+    if (g.warp == g.w0) {
       double s = 0.0;
-#pragma unroll
-      for (int v = 0; v < kWarps; ++v) s += red[v * 32 + g.lane];
-      red_cta[g.lane] = s;
+      for (int v = g.w0; v < g.w0 + g.nwl; ++v) s += red[v * 32 + g.lane];
+      red_cta[32 * g.slot + g.lane] = s;
     }
     g.sync();
     if (g.gw == 0) {
-      double part = red_cta[g.lane];
+      double part = red_cta[32 * g.slot + g.lane];
       if (g.cluster) {
         cg::cluster_group c = cg::this_cluster();
         for (int r = 1; r < g.size; ++r) part += c.map_shared_rank(red_cta, r)[g.lane];
       }
       const double rhs = g.lane < w ? ldx<CL>(xs + kb + g.lane) - part : 0.0;
-      backward_triangle(L, nr, kb, w, rhs, xs, g.lane);
+      backward_triangle<CL>(L, nr, kb, w, rhs, xs, rd_off, g.lane);
     }
     g.sync();
   }
 }
 
-// The whole implicit application for one subdomain by one group (CL: the
-// cluster; x is then read past L1).  Per etree level, by its supernode count
-// c: c >= half the group's warps -- one warp per supernode; else c >= the
-// group's CTAs -- one CTA per supernode (the CTA's warps share its panel
-// rows); else (the top separators) one supernode at a time on the whole
-// group.  One group barrier per level, two per 32-column block in the last case.
+// L2 prefetch of what level `lev` reads first (its supernodes' descriptors,
+// L panels and pruned-row lists), spread over the group's warps: issued at
+// the top of the level before, so that the level's dependent loads (a
+// descriptor, then its panel, then the rows it updates) hit L2 instead of
+// HBM.  A prefetch only moves data into the cache; it changes no value.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ void prefetch_level(const Group &g, const IPtrs &P, int lev, const double *__restrict__ Lv) {
+  const int a = P.levptr[lev], b = P.levptr[lev + 1];
+  for (int s = a + g.gw; s < b; s += g.nw) {
+    const ISn sn = P.sns[s];
+    const int nr = sn.ns + sn.rs;
+    const char *lo = reinterpret_cast<const char *>(Lv + sn.lval);
+    const char *hi = reinterpret_cast<const char *>(Lv + sn.lval + col_off(sn.ns, nr));
+    const char *first = reinterpret_cast<const char *>(reinterpret_cast<uintptr_t>(lo) & ~uintptr_t(127));
+    for (const char *q = first + 128 * g.lane; q < hi; q += 128 * 32) prefetch_l2(q);
+    if (g.lane == 0 && sn.rs > 0) prefetch_l2(P.rows + sn.rows_off);
+  }
+  // the descriptors (32 bytes each; four to a line), inside the level's range
+  for (int k = a + 4 * (32 * g.gw + g.lane); k < b; k += 4 * 32 * g.nw) prefetch_l2(P.sns + k);
+}
+
+// The levels [lev_lo, lev_lo + n_lev) of a subdomain by one group (CL: x
+// read past L1).  Per etree level, by its supernode count c: c >= half the
+// group's warps -- one warp per supernode; else c >= the group's CTAs -- one
+// CTA per supernode (the CTA's warps share its panel rows); else (the top
+// separators) one supernode at a time on the whole group.  One group barrier
+// per level, two per 32-column block in the last case.
 template <bool CL>
-__device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, const double *__restrict__ Lv,
-                                const double *__restrict__ lam, double *q, double *X, uint32_t *status,
-                                double (*ys)[32], double *red, double *red_cta) {
-  const int tid = g.warp * 32 + g.lane;
-  const int gt = g.rank * kThreadsI + tid, nt = g.size * kThreadsI;
+__device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n_lev, const double *__restrict__ Lv,
+                               double *x, double (*ys)[32]) {
+  const int64_t rd = P.rd_off;
   const Group cta = cta_group(g.warp, g.lane);
-  double *x = X + sd.x_off;
-  // x = 0, then x = B^T lambda
+  if (n_lev > 0) prefetch_level(g, P, lev_lo, Lv);
+  for (int l = 0; l < n_lev; ++l) {
+    if (l + 1 < n_lev) prefetch_level(g, P, lev_lo + l + 1, Lv);
+    const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
+    if (2 * (b - a) >= g.nw) {
+      for (int s = a + g.gw; s < b; s += g.nw) forward_warp<CL>(P.sns[s], Lv, P.rows, x, ys[g.warp], rd, g.lane);
+      g.sync();
+    } else if (!g.cluster && b - a >= 2) {
+      // 2 .. 7 supernodes on one CTA: each on its own subgroup of the warps, side by side
+      const int c = b - a, j = g.warp * c / kWarps, w0 = (kWarps * j + c - 1) / c;
+      const Group sg = sub_group(g.warp, g.lane, w0, (kWarps * (j + 1) + c - 1) / c - w0, j);
+      forward_group<CL>(sg, P.sns[a + j], Lv, P.rows, x, ys[g.warp], rd);
+      __syncthreads();
+    } else if (b - a >= g.size) {
+      for (int s = a + g.rank; s < b; s += g.size) forward_group<CL>(cta, P.sns[s], Lv, P.rows, x, ys[g.warp], rd);
+      if (g.cluster) g.sync();
+    } else {
+      for (int s = a; s < b; ++s) forward_group<CL>(g, P.sns[s], Lv, P.rows, x, ys[g.warp], rd);
+    }
+  }
+}
+
+template <bool CL>
+__device__ void backward_levels(const Group &g, const IPtrs &P, int lev_lo, int n_lev,
+                                const double *__restrict__ Lv, double *x, double *red, double *red_cta) {
+  const int64_t rd = P.rd_off;
+  const Group cta = cta_group(g.warp, g.lane);
+  for (int l = n_lev - 1; l >= 0; --l) {
+    if (l > 0) prefetch_level(g, P, lev_lo + l - 1, Lv);
+    const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
+    if (2 * (b - a) >= g.nw) {
+      for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, rd, g.lane);
+      g.sync();
+    } else if (!g.cluster && b - a >= 2) {
+      const int c = b - a, j = g.warp * c / kWarps, w0 = (kWarps * j + c - 1) / c;
+      const Group sg = sub_group(g.warp, g.lane, w0, (kWarps * (j + 1) + c - 1) / c - w0, j);
+      backward_group<CL>(sg, P.sns[a + j], Lv, P.rows, x, rd, red, red_cta);
+      __syncthreads();
+    } else if (b - a >= g.size) {
+      for (int s = a + g.rank; s < b; s += g.size) backward_group<CL>(cta, P.sns[s], Lv, P.rows, x, rd, red, red_cta);
+      if (g.cluster) g.sync();
+    } else {
+      for (int s = a; s < b; ++s) backward_group<CL>(g, P.sns[s], Lv, P.rows, x, rd, red, red_cta);
+    }
+  }
+}
+
+// 1 / d for a diagonal entry d; ok: d positive and finite (tested on the bit
+// pattern).  In single precision's range by Newton's iteration for the
+// reciprocal, r <- r + r (1 - d r), from the single-precision reciprocal of d:
+// two steps take its 24 correct bits past FP64's 53 (four FMAs and two
+// conversions against the longer sequence of an FP64 division); otherwise a
+// division.
+__device__ __forceinline__ double pos_recip(double d, bool &ok) {
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  ok = b > 0 && ex < 0x7FF;
+  if (ex > 1023 - 120 && ex < 1023 + 120) {
+    double r = (double)__frcp_rn(__double2float_rn(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+  }
+  return 1.0 / d;
+}
+
+// x = B^T lambda for one subdomain (threads gt of nt), and the reciprocal
+// diagonal 1 / L(c, c) of every column of its visited supernodes (once per
+// call, all lanes busy, instead of a division per block in the solves); a
+// diagonal entry that is not positive and finite sets status bit 0.
+__device__ void gather_x(const IPtrs &P, const ISub &sd, const double *__restrict__ Lv,
+                         const double *__restrict__ lam, double *x, int gt, int nt, const Group &g,
+                         uint32_t *status) {
   for (int c = gt; c < sd.n; c += nt) x[c] = 0.0;
+  double *rd = x + P.rd_off;
+  for (int s = sd.sn_lo + gt / 32; s < sd.sn_hi; s += nt / 32) {
+    const ISn sn = P.sns[s];
+    const int nr = sn.ns + sn.rs;
+    for (int t = gt & 31; t < sn.ns; t += 32) {
+      bool ok;
+      const double r = pos_recip(Lv[sn.lval + col_off(t, nr)], ok);
+      if (!ok) atomicOr(status, 1u);
+      rd[sn.c0 + t] = ok ? r : 0.0;
+    }
+  }
   g.sync();
   for (int r = sd.g_lo + gt; r < sd.g_hi; r += nt) {
     const IRow row = P.grow[r];
@@ -373,52 +518,93 @@ __device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, 
     for (int e = row.e_lo; e < row.e_hi; ++e) v += P.gent[e].sign * lam[P.gent[e].gj];
     x[row.r] = v;
   }
-  g.sync();
-  for (int l = 0; l < sd.n_lev; ++l) {
-    const int a = P.levptr[sd.lev_lo + l], b = P.levptr[sd.lev_lo + l + 1];
-    if (2 * (b - a) >= g.nw) {
-      for (int s = a + g.gw; s < b; s += g.nw) forward_warp<CL>(P.sns[s], Lv, P.rows, x, ys[g.warp], status, g.lane);
-      g.sync();
-    } else if (b - a >= g.size) {
-      for (int s = a + g.rank; s < b; s += g.size) forward_group<CL>(cta, P.sns[s], Lv, P.rows, x, ys[g.warp], status);
-      if (g.cluster) g.sync();
-    } else {
-      for (int s = a; s < b; ++s) forward_group<CL>(g, P.sns[s], Lv, P.rows, x, ys[g.warp], status);
-    }
-  }
-  for (int l = sd.n_lev - 1; l >= 0; --l) {
-    const int a = P.levptr[sd.lev_lo + l], b = P.levptr[sd.lev_lo + l + 1];
-    if (2 * (b - a) >= g.nw) {
-      for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, g.lane);
-      g.sync();
-    } else if (b - a >= g.size) {
-      for (int s = a + g.rank; s < b; s += g.size) backward_group<CL>(cta, P.sns[s], Lv, P.rows, x, red, red_cta);
-      if (g.cluster) g.sync();
-    } else {
-      for (int s = a; s < b; ++s) backward_group<CL>(g, P.sns[s], Lv, P.rows, x, red, red_cta);
-    }
-  }
-  for (int e = sd.s_lo + gt; e < sd.s_hi; e += nt) {
+}
+
+template <bool CL>
+__device__ void scatter_q(const IPtrs &P, int e_lo, int e_hi, const double *x, double *q, int gt, int nt) {
+  for (int e = e_lo + gt; e < e_hi; e += nt) {
     const ISEnt t = P.sent[e];
     atomicAdd(q + t.gj, t.sign * ldx<CL>(x + t.r));
   }
 }
 
-// Launched in clusters of kCluster CTAs.  An item is either one large
-// subdomain solved by the whole cluster, or up to kCluster small subdomains,
-// one per CTA.
+// The whole implicit application for one subdomain by one group (the
+// cluster, or one CTA).
+template <bool CL>
+__device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, const double *__restrict__ Lv,
+                                const double *__restrict__ lam, double *q, double *X, uint32_t *status,
+                                double (*ys)[32], double *red, double *red_cta) {
+  const int tid = g.warp * 32 + g.lane;
+  const int gt = g.rank * kThreadsI + tid, nt = g.size * kThreadsI;
+  double *x = X + sd.x_off;
+  gather_x(P, sd, Lv, lam, x, gt, nt, g, status);
+  g.sync();
+  forward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, ys);
+  backward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, red, red_cta);
+  scatter_q<CL>(P, sd.s_lo, sd.s_hi, x, q, gt, nt);
+}
+
+// Item kind 2: subdomain sub[j] on the CTA pair (2j, 2j + 1) of a cluster;
+// CTA 2j + part solves subtree part (0: A, 1: B), the first CTA of the pair
+// also the top chain.  Every CTA of the cluster passes the same three
+// cluster barriers:
+//   S1 after the first CTA's gather of x = B^T lambda (the second CTA reads
+//      its rows afterwards, first touch of those lines on its SM);
+//   S2 after both subtrees' forward solves (their updates of the top rows
+//      are atomic in L2) -- then the first CTA solves the top forward and
+//      backward, reading x past L1;
+//   S3 after the top -- then each CTA solves its subtree backward (ancestor
+//      rows of the top read past L1) and scatters its own rows.
+// The subtrees share no rows, so between the barriers each CTA only reads
+// rows that it or its own warps wrote, or that were complete at a barrier.
+__device__ void solve_pair_item(const IItem &it, const IPtrs &P, const double *__restrict__ Lv,
+                                const double *__restrict__ lam, double *q, double *X, uint32_t *status,
+                                double (*ys)[32], double *red, double *red_cta, int warp, int lane) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank(), j = r >> 1, part = r & 1;
+  const bool act = j < it.n;
+  const Group cta = cta_group(warp, lane);
+  const int tid = warp * 32 + lane;
+  ISub sd{};
+  if (act) sd = P.subs[it.sub[j]];
+  double *x = X + sd.x_off;
+  const int lev_part = part == 0 ? sd.lev_lo : sd.lev_lo + sd.n_lev_a;
+  const int n_part = part == 0 ? sd.n_lev_a : sd.n_lev_b;
+  const int lev_top = sd.lev_lo + sd.n_lev_a + sd.n_lev_b, n_top = sd.n_lev - sd.n_lev_a - sd.n_lev_b;
+  if (act && part == 0) gather_x(P, sd, Lv, lam, x, tid, kThreadsI, cta, status);
+  cl.sync();                                                             // S1
+  if (act) forward_levels<false>(cta, P, lev_part, n_part, Lv, x, ys);
+  cl.sync();                                                             // S2
+  if (act && part == 0) {
+    forward_levels<true>(cta, P, lev_top, n_top, Lv, x, ys);
+    backward_levels<true>(cta, P, lev_top, n_top, Lv, x, red, red_cta);
+    scatter_q<true>(P, sd.s_mid2, sd.s_hi, x, q, tid, kThreadsI);
+  }
+  cl.sync();                                                             // S3
+  if (act) {
+    backward_levels<true>(cta, P, lev_part, n_part, Lv, x, red, red_cta);
+    if (part == 0) scatter_q<true>(P, sd.s_lo, sd.s_mid1, x, q, tid, kThreadsI);
+    else scatter_q<true>(P, sd.s_mid1, sd.s_mid2, x, q, tid, kThreadsI);
+  }
+}
+
+// Launched in clusters of kCluster CTAs.  An item is one large subdomain
+// solved by the whole cluster, up to kCluster small subdomains (one per
+// CTA), or up to kCluster / 2 subdomains on CTA pairs.
 __global__ void __launch_bounds__(kThreadsI, 1) implicit_kernel(const IPtrs P, const double *__restrict__ Lv,
                                                                 const double *__restrict__ lam, double *q,
                                                                 double *X, uint32_t *status) {
   __shared__ double ys[kWarps][32];
   __shared__ double red[kWarps * 32];
-  __shared__ double red_cta[32];
+  __shared__ double red_cta[kWarps * 32];          // one 32-double row per (sub)group
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const IItem it = P.items[blockIdx.x / kCluster];
   if (it.kind == 0) {
     const Group g = cluster_group(warp, lane);
     solve_subdomain<true>(g, P, P.subs[it.sub[0]], Lv, lam, q, X, status, ys, red, red_cta);
     cg::this_cluster().sync();   // no CTA leaves while the first one may read its shared memory
+  } else if (it.kind == 2) {
+    solve_pair_item(it, P, Lv, lam, q, X, status, ys, red, red_cta, warp, lane);
   } else {
     const int r = (int)(blockIdx.x % kCluster);   // also without a cluster launch
     if (r < it.n) {
@@ -440,6 +626,8 @@ struct sci_ctx {
   void *plan_dev = nullptr;
   size_t plan_dev_bytes = 0;
   int64_t n_items = 0;
+  int64_t n_pair_subdomains = 0;    // subdomains on CTA pairs (the launch then needs clusters)
+  int64_t x_total = 0;              // doubles of all subdomains' x (the reciprocal diagonals follow)
 
   IPtrs ptrs() const {
     const uint8_t *b = static_cast<const uint8_t *>(plan_dev);
@@ -452,6 +640,7 @@ struct sci_ctx {
     p.gent = reinterpret_cast<const IEnt *>(b + hdr.sec_off[5]);
     p.sent = reinterpret_cast<const ISEnt *>(b + hdr.sec_off[6]);
     p.items = reinterpret_cast<const IItem *>(b + hdr.sec_off[7]);
+    p.rd_off = x_total;
     return p;
   }
 };
@@ -471,7 +660,57 @@ sc_status ifail(sci_ctx *c, sc_status st, const std::string &m) {
   return st;
 }
 
-sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t cluster_min_work) {
+// The two parts of a subdomain's visited etree forest for a CTA pair.  From
+// the roots down: the current set of subtrees is dealt, largest first, to the
+// lighter of two parts; if the lighter one gets at least a fifth of the set's
+// work, those are the parts.  Otherwise the largest subtree's root and the
+// other (small) subtrees go to the top -- a regularised fixed dof, for one,
+// is a one-column tree of its own -- and the search goes on in the largest
+// subtree's children.  part[s] = 0 / 1 / 2 (top); false if no split is found.
+bool split_tree(const sc::SubPlan &S, const std::vector<int32_t> &vis, std::vector<int8_t> &part) {
+  const int32_t nsn = (int32_t)S.sn_c0.size();
+  std::vector<std::vector<int32_t>> ch(nsn);
+  std::vector<int32_t> roots;
+  std::vector<int64_t> w(nsn, 0);
+  for (int32_t s : vis) {                       // vis: children before parents
+    w[s] += (int64_t)S.sn_ns[s] * (S.sn_ns[s] + 1) / 2 + (int64_t)S.sn_ns[s] * S.sn_rs[s];
+    if (S.sparent[s] >= 0) {
+      ch[S.sparent[s]].push_back(s);
+      w[S.sparent[s]] += w[s];
+    } else {
+      roots.push_back(s);
+    }
+  }
+  part.assign(nsn, 2);
+  std::vector<int32_t> cur = roots;
+  while (!cur.empty()) {
+    std::stable_sort(cur.begin(), cur.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
+    int64_t load[2] = {0, 0};
+    std::vector<int8_t> side(cur.size());
+    for (size_t k = 0; k < cur.size(); ++k) {
+      side[k] = load[0] <= load[1] ? 0 : 1;
+      load[side[k]] += w[cur[k]];
+    }
+    if (cur.size() >= 2 && 5 * std::min(load[0], load[1]) >= load[0] + load[1]) {
+      std::vector<int32_t> stack;
+      for (size_t k = 0; k < cur.size(); ++k) {
+        stack.assign(1, cur[k]);
+        while (!stack.empty()) {
+          const int32_t v = stack.back();
+          stack.pop_back();
+          part[v] = side[k];
+          for (int32_t u : ch[v]) stack.push_back(u);
+        }
+      }
+      return true;
+    }
+    cur = ch[cur[0]];                             // the rest of this set stays in the top
+  }
+  return false;
+}
+
+sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t cluster_min_work,
+                int32_t pairs) {
   for (int32_t i = 0; i < nsub; ++i)
     if (d[i].Bt_val)
       return ifail(ctx, SC_ERR_INVALID_ARG, "subdomain " + std::to_string(i) + ": sci_plan takes signed-Boolean B^T (Bt_val must be NULL)");
@@ -505,6 +744,13 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
   std::vector<int32_t> order(nsub);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+  if (cluster_min_work < 0)
+    cluster_min_work = std::max<int64_t>(1, 2 * nnz_all / std::max<int64_t>(1, std::min<int64_t>(kCtaSlots, nsub)) + 1);
+  // CTA pairs only on request: measured on GB300 (config 2, 64 subdomains on
+  // 152 SMs) a pair took 2.51 ms against 2.20 ms for one CTA per subdomain --
+  // the subtrees are not the critical path, the per-level chains are
+  const bool want_pairs = pairs == 1;
+  std::vector<int8_t> is_pair(nsub, 0);
   for (int32_t i : order) {
     const sc::SubPlan &S = P[i];
     const sc_subdomain_desc &D = d[i];
@@ -515,17 +761,27 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
       vis.push_back(s);
       if (S.sparent[s] >= 0) h[S.sparent[s]] = std::max(h[S.sparent[s]], h[s] + 1);
     }
-    std::stable_sort(vis.begin(), vis.end(), [&](int32_t a, int32_t b) { return h[a] < h[b]; });
+    std::vector<int8_t> part;
+    const bool pair = want_pairs && work[i] < cluster_min_work && split_tree(S, vis, part);
+    if (!pair) part.assign(nsn, 2);
+    is_pair[i] = pair;
+    // (part, level, first column): parts A, B, then the top; one level sequence each
+    std::stable_sort(vis.begin(), vis.end(), [&](int32_t a, int32_t b) {
+      return part[a] != part[b] ? part[a] < part[b] : h[a] < h[b];
+    });
     ISub sd{};
     sd.x_off = x_off[i];
     sd.n = D.n;
     sd.sn_lo = (int32_t)sns.size();
     sd.lev_lo = (int32_t)levptr.size();
-    int32_t cur = -1;
+    int32_t cur_part = -1, cur_h = -1, nlev = 0, nlev_part[3] = {0, 0, 0};
     for (int32_t s : vis) {
-      while (cur < h[s]) {
+      if (part[s] != cur_part || h[s] != cur_h) {   // a new level (heights are increasing within a part)
         levptr.push_back((int32_t)sns.size());
-        ++cur;
+        cur_part = part[s];
+        cur_h = h[s];
+        ++nlev;
+        ++nlev_part[cur_part];
       }
       ISn sn{};
       const int32_t c0 = S.sn_c0[s], ns = S.sn_ns[s], rs = S.sn_rs[s];
@@ -540,16 +796,26 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
       sns.push_back(sn);
     }
     sd.sn_hi = (int32_t)sns.size();
-    sd.n_lev = cur + 1;
+    sd.n_lev = nlev;
+    sd.n_lev_a = nlev_part[0];
+    sd.n_lev_b = nlev_part[1];
     levptr.push_back(sd.sn_hi);
     max_lev = std::max<int64_t>(max_lev, sd.n_lev);
     // B^T by row (gather) and by entry (scatter)
     std::vector<std::pair<int32_t, int32_t>> ent;   // (row, entry index)
+    std::vector<ISEnt> by_part[3];                    // scatter entries by the part of their row
     for (int32_t j = 0; j < D.m; ++j)
       for (int32_t e = D.Bt_colptr[j]; e < D.Bt_colptr[j + 1]; ++e) {
         ent.emplace_back(D.Bt_rowind[e], e);
-        sent.push_back(ISEnt{D.Bt_rowind[e], D.lambda_map[j], (int32_t)D.Bt_sign[e], 0});
+        const int32_t r = D.Bt_rowind[e];
+        by_part[part[S.snode_of[r]]].push_back(ISEnt{r, D.lambda_map[j], (int32_t)D.Bt_sign[e], 0});
       }
+    sd.s_lo = (int32_t)sent.size();
+    sent.insert(sent.end(), by_part[0].begin(), by_part[0].end());
+    sd.s_mid1 = (int32_t)sent.size();
+    sent.insert(sent.end(), by_part[1].begin(), by_part[1].end());
+    sd.s_mid2 = (int32_t)sent.size();
+    sent.insert(sent.end(), by_part[2].begin(), by_part[2].end());
     std::vector<int32_t> col_of(ent.size());
     for (int32_t j = 0; j < D.m; ++j)
       for (int32_t e = D.Bt_colptr[j]; e < D.Bt_colptr[j + 1]; ++e) col_of[e] = j;
@@ -569,7 +835,6 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
     }
     sd.g_hi = (int32_t)grow.size();
     sd.s_hi = (int32_t)sent.size();
-    sd.s_lo = sd.s_hi - (int32_t)ent.size();
     subs.push_back(sd);
   }
   // items: subdomains with at least cluster_min_work visited entries get a
@@ -579,8 +844,7 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
   // of the CTAs the batch can occupy (measured on GB300: clusters shorten a
   // heavy tail of a few large subdomains, but cost more than they give on a
   // batch of similar ones)
-  if (cluster_min_work < 0)
-    cluster_min_work = std::max<int64_t>(1, 2 * nnz_all / std::max<int64_t>(1, std::min<int64_t>(kCtaSlots, nsub)) + 1);
+  // pairs: kCluster / 2 subdomains to a cluster, one per CTA pair
   std::vector<IItem> items;
   for (int32_t k = 0; k < nsub;) {
     IItem it{};
@@ -588,19 +852,28 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
       it.kind = 0;
       it.n = 1;
       it.sub[0] = k++;
+    } else if (is_pair[order[k]]) {
+      it.kind = 2;
+      while (it.n < kCluster / 2 && k < nsub && is_pair[order[k]] && work[order[k]] < cluster_min_work)
+        it.sub[it.n++] = k++;
     } else {
       it.kind = 1;
-      while (it.n < kCluster && k < nsub) it.sub[it.n++] = k++;
+      while (it.n < kCluster && k < nsub && !is_pair[order[k]] && work[order[k]] < cluster_min_work)
+        it.sub[it.n++] = k++;
     }
     items.push_back(it);
   }
   ctx->n_items = (int64_t)items.size();
   int64_t n_big = 0;
-  for (const IItem &it : items) n_big += it.kind == 0;
+  ctx->n_pair_subdomains = 0;
+  for (const IItem &it : items) {
+    n_big += it.kind == 0;
+    if (it.kind == 2) ctx->n_pair_subdomains += it.n;
+  }
   IHeader &H = ctx->hdr;
   H = IHeader{};
   H.magic = 0x50494353u;   // "SCIP"
-  H.version = 1;
+  H.version = 2;
   H.nsub = nsub;
   H.n_sn = (int64_t)sns.size();
   H.n_levptr = (int64_t)levptr.size();
@@ -623,7 +896,9 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
   std::memcpy(blob.data(), &H, sizeof(H));
   sci_sizes &z = ctx->sizes;
   z.plan_bytes = blob.size();
-  z.ws_bytes = 256 + sizeof(double) * (size_t)x_off[nsub];
+  // status word, every subdomain's x, then its reciprocal diagonals at the same offsets
+  ctx->x_total = x_off[nsub];
+  z.ws_bytes = 256 + 2 * sizeof(double) * (size_t)x_off[nsub];
   z.L_values = L_off[nsub];
   z.n_supernodes = (int64_t)sns.size();
   z.nnz_visited = nnz_all;
@@ -650,7 +925,8 @@ sc_status sci_plan(sci_ctx **out, int32_t nsub, const sc_subdomain_desc *subdoma
   ctx->nsub = nsub;
   ctx->n_dual = n_dual;
   try {
-    return build(ctx, nsub, subdomains, opt ? opt->cluster_min_work : -1);
+    if (opt && (opt->pairs < -1 || opt->pairs > 1)) return ifail(ctx, SC_ERR_INVALID_ARG, "pairs must be -1, 0 or 1");
+    return build(ctx, nsub, subdomains, opt ? opt->cluster_min_work : -1, opt ? opt->pairs : 0);
   } catch (const std::bad_alloc &) {
     return ifail(ctx, SC_ERR_OOM, "host allocation failed while planning");
   } catch (...) {
@@ -704,7 +980,8 @@ sc_status sci_apply(sci_ctx *ctx, const double *L_values_dev, const double *lamb
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = ctx->sizes.n_cluster_subdomains > 0 ? 1 : 0;   // no cluster when no item needs one
+    // no cluster when no item needs one (pair items synchronise their cluster)
+    cfg.numAttrs = ctx->sizes.n_cluster_subdomains > 0 || ctx->n_pair_subdomains > 0 ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, implicit_kernel, ctx->ptrs(), L_values_dev, lambda_dev, q_dev, X, status);
   }
   if (e != cudaSuccess) return ifail(ctx, SC_ERR_CUDA, std::string("sci_apply: ") + cudaGetErrorString(e));

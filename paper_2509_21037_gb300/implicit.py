@@ -17,9 +17,10 @@ class ImplicitPlan:
     """sci_plan + its device buffers, for a list of factored subdomains
     (the objects :class:`paper_2509_21037_gb300.sc.Plan` takes).
     cluster_min_work: -1 automatic, 0 every subdomain on an 8-CTA cluster,
-    a large value none (include/sc_implicit.h, sci_options)."""
+    a large value none; pairs: 0 automatic, 1 every subdomain whose tree
+    splits on a CTA pair, -1 none (include/sc_implicit.h, sci_options)."""
 
-    def __init__(self, subdomains: Sequence, n_dual: int, cluster_min_work: int = -1):
+    def __init__(self, subdomains: Sequence, n_dual: int, cluster_min_work: int = -1, pairs: int = 0):
         self.lib = _native.sc_lib()
         self.nsub = len(subdomains)
         self.n_dual = int(n_dual)
@@ -37,6 +38,7 @@ class ImplicitPlan:
         h = ctypes.c_void_p()
         opt = abi.ImplicitOptions()
         opt.cluster_min_work = int(cluster_min_work)
+        opt.pairs = int(pairs)
         st = self.lib.sci_plan(ctypes.byref(h), self.nsub, descs, self.n_dual, ctypes.byref(opt))
         self.h = h
         if st != abi.SC_OK:

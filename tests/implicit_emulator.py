@@ -16,7 +16,7 @@ HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("nsub", "<i4"), ("pad"
                    ("n_gent", "<i8"), ("n_sent", "<i8"), ("n_items", "<i8"), ("sec_off", "<u8", 8)])
 SUB = np.dtype([("x_off", "<i8"), ("n", "<i4"), ("sn_lo", "<i4"), ("sn_hi", "<i4"), ("lev_lo", "<i4"),
                 ("n_lev", "<i4"), ("g_lo", "<i4"), ("g_hi", "<i4"), ("s_lo", "<i4"), ("s_hi", "<i4"),
-                ("pad", "<i4")])
+                ("n_lev_a", "<i4"), ("n_lev_b", "<i4"), ("s_mid1", "<i4"), ("s_mid2", "<i4"), ("pad", "<i4")])
 SN = np.dtype([("lval", "<i8"), ("rows_off", "<i8"), ("c0", "<i4"), ("ns", "<i4"), ("rs", "<i4"),
                ("sub", "<i4")])
 GROW = np.dtype([("r", "<i4"), ("e_lo", "<i4"), ("e_hi", "<i4"), ("pad", "<i4")])
@@ -31,7 +31,7 @@ SECTIONS = [("subs", SUB, "nsub"), ("sns", SN, "n_sn"), ("levptr", "<i4", "n_lev
 def export_plan(iplan) -> dict:
     blob = iplan.export_plan()
     h = np.frombuffer(blob[:HEADER.itemsize].tobytes(), HEADER)[0]
-    assert h["magic"] == 0x50494353 and h["version"] == 1
+    assert h["magic"] == 0x50494353 and h["version"] == 2
     out = {"header": h}
     for k, (name, dt, cnt) in enumerate(SECTIONS):
         off = int(h["sec_off"][k])
@@ -80,10 +80,49 @@ def check_bounds(T: dict, sizes, L_offsets, n_dual: int) -> None:
     # cluster items cover every subdomain exactly once
     covered = []
     for it in T["items"]:
-        assert it["kind"] in (0, 1) and 1 <= it["n"] <= 8
-        assert it["kind"] == 1 or it["n"] == 1
+        assert it["kind"] in (0, 1, 2) and 1 <= it["n"] <= 8
+        assert it["kind"] != 0 or it["n"] == 1
+        assert it["kind"] != 2 or it["n"] <= 4
         covered += [int(v) for v in it["sub"][:it["n"]]]
+        if it["kind"] == 2:
+            for v in it["sub"][:it["n"]]:
+                check_pair_split(T, subs[int(v)])
     assert sorted(covered) == list(range(len(subs)))
+
+
+def _parts(T: dict, sd) -> list:
+    """Supernode index ranges of parts A, B and the top of a pair subdomain."""
+    lev = T["levptr"]
+    la, na, nb, n = int(sd["lev_lo"]), int(sd["n_lev_a"]), int(sd["n_lev_b"]), int(sd["n_lev"])
+    return [range(lev[la], lev[la + na]), range(lev[la + na], lev[la + na + nb]),
+            range(lev[la + na + nb], lev[la + n])]
+
+
+def check_pair_split(T: dict, sd) -> None:
+    """What the CTA pair's three barriers rely on: parts A and B are non-empty
+    and touch disjoint rows of x (each part's supernodes update only their own
+    part's or the top's rows; the top updates only top rows), and the scatter
+    ranges [s_lo, s_mid1), [s_mid1, s_mid2), [s_mid2, s_hi) hold rows of A, B
+    and the top."""
+    sns, rows = T["sns"], T["rows"]
+    parts = _parts(T, sd)
+    assert len(parts[0]) > 0 and len(parts[1]) > 0
+    owner = np.full(int(sd["n"]), -1)
+    for p, rg in enumerate(parts):
+        for s in rg:
+            c0, ns = int(sns[s]["c0"]), int(sns[s]["ns"])
+            assert np.all(owner[c0:c0 + ns] == -1)
+            owner[c0:c0 + ns] = p
+    for p, rg in enumerate(parts):
+        for s in rg:
+            sn = sns[s]
+            R = rows[sn["rows_off"]:sn["rows_off"] + sn["rs"]]
+            allowed = (p, 2) if p < 2 else (2,)
+            assert np.all(np.isin(owner[R], allowed)), "a part updates rows of the other part"
+    for p, (lo, hi) in enumerate([(sd["s_lo"], sd["s_mid1"]), (sd["s_mid1"], sd["s_mid2"]), (sd["s_mid2"], sd["s_hi"])]):
+        assert sd["s_lo"] <= lo <= hi <= sd["s_hi"]
+        for e in T["sent"][lo:hi]:
+            assert owner[e["r"]] == p
 
 
 def emulate(T: dict, sizes, Lv: np.ndarray, lam: np.ndarray, n_dual: int) -> np.ndarray:

@@ -408,13 +408,43 @@ def test_implicit_cluster_items():
     Loff = np.concatenate([[0], np.cumsum([f.L.values.size for f in fs])])
     nnz = implicit.ImplicitPlan(fs, prob.n_dual).sizes.nnz_visited
     for cmw, kinds in ((0, {0}), (1 << 60, {1}), (1, {0}), (nnz // 40, {0, 1})):
-        ip = implicit.ImplicitPlan(fs, prob.n_dual, cluster_min_work=cmw)
+        ip = implicit.ImplicitPlan(fs, prob.n_dual, cluster_min_work=cmw, pairs=-1)
         T = ie.export_plan(ip)
         ie.check_bounds(T, ip.sizes, Loff, prob.n_dual)
         got = set(int(k) for k in T["items"]["kind"])
         if kinds is not None:
             assert got == kinds, (cmw, got)
         assert ip.sizes.n_cluster_subdomains == int(np.sum(T["items"]["kind"] == 0))
+
+
+def test_implicit_pair_items():
+    """CTA pairs (on request): every pair subdomain splits into two non-empty
+    parts touching disjoint rows, with the scatter grouped by part
+    (check_pair_split); the plan replayed in its level order reproduces the
+    oracle; the automatic rule keeps one CTA per subdomain; invalid option
+    values are refused."""
+    prob = synth.mixed_batch(lat2d=(4, 4), k2d=(6, 40), lat3d=(2, 2, 1), k3d=(2, 6), seed=2)
+    fs = host.factorize_problem(prob.subdomains)
+    Loff = np.concatenate([[0], np.cumsum([f.L.values.size for f in fs])])
+    lam = np.random.default_rng(4).standard_normal(prob.n_dual)
+    Lv = np.concatenate([f.L.values for f in fs])
+    qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains, refine=1), [s.lambda_map for s in prob.subdomains],
+                           lam, prob.n_dual)
+    for pairs in (0, 1):
+        ip = implicit.ImplicitPlan(fs, prob.n_dual, cluster_min_work=1 << 60, pairs=pairs)
+        T = ie.export_plan(ip)
+        ie.check_bounds(T, ip.sizes, Loff, prob.n_dual)
+        kinds = set(int(k) for k in T["items"]["kind"])
+        if pairs == 0:
+            assert kinds == {1}, kinds
+            continue
+        assert 2 in kinds, kinds
+        npair = sum(int(it["n"]) for it in T["items"] if it["kind"] == 2)
+        assert npair >= len(fs) // 2
+        q = ie.emulate(T, ip.sizes, Lv, lam, prob.n_dual)
+        assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+    with pytest.raises(sc.SCError, match="pairs"):
+        implicit.ImplicitPlan(fs, prob.n_dual, pairs=2)
 
 
 def test_implicit_plan_subdomain_order_and_validation():

@@ -25,8 +25,8 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _implicit_q(fs, n_dual, lam, dev, cluster_min_work=-1):
-    ip = implicit.ImplicitPlan(fs, n_dual, cluster_min_work=cluster_min_work).upload(dev)
+def _implicit_q(fs, n_dual, lam, dev, cluster_min_work=-1, pairs=0):
+    ip = implicit.ImplicitPlan(fs, n_dual, cluster_min_work=cluster_min_work, pairs=pairs).upload(dev)
     Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
     lam_d = torch.from_numpy(lam).to(dev)
     q = torch.full((max(1, n_dual),), float("nan"), dtype=torch.float64, device=dev)
@@ -61,17 +61,21 @@ def test_implicit_matches_oracle(name, prob, dev):
     assert err <= TOL
 
 
-@pytest.mark.parametrize("mode", ["all_clusters", "no_clusters", "mixed"])
+@pytest.mark.parametrize("mode", ["all_clusters", "no_clusters", "mixed", "pairs", "mixed_pairs"])
 def test_implicit_cluster_modes(mode, dev):
-    """Every subdomain on an 8-CTA cluster, every subdomain on one CTA, and a
-    mix (large ones on clusters, small ones packed one per CTA): same q."""
+    """Every subdomain on an 8-CTA cluster, every subdomain on one CTA, a mix
+    (large ones on clusters, small ones packed one per CTA), every subdomain
+    on a CTA pair (its two subtrees solved side by side), and large ones on
+    clusters with the rest on pairs: same q."""
     prob = synth.mixed_batch(lat2d=(4, 4), k2d=(6, 40), lat3d=(2, 2, 1), k3d=(2, 8), seed=2)
     fs = host.factorize_problem(prob.subdomains)
     nnz = implicit.ImplicitPlan(fs, prob.n_dual).sizes.nnz_visited
-    cmw = {"all_clusters": 0, "no_clusters": 1 << 60, "mixed": nnz // 40}[mode]
+    cmw = {"all_clusters": 0, "no_clusters": 1 << 60, "mixed": nnz // 40, "pairs": 1 << 60,
+           "mixed_pairs": nnz // 40}[mode]
+    pairs = 1 if mode in ("pairs", "mixed_pairs") else -1
     lam = np.random.default_rng(4).standard_normal(prob.n_dual)
-    ip, q = _implicit_q(fs, prob.n_dual, lam, dev, cmw)
-    if mode == "mixed":
+    ip, q = _implicit_q(fs, prob.n_dual, lam, dev, cmw, pairs)
+    if mode.startswith("mixed"):
         assert 0 < ip.sizes.n_cluster_subdomains < len(fs)
     err = _rel(q, _oracle_q(prob.subdomains, lam, prob.n_dual, refine=1))
     print(f"cluster mode {mode}: {ip.sizes.n_cluster_subdomains} of {len(fs)} on clusters, error {err:.3e}")
@@ -107,6 +111,7 @@ def test_implicit_equals_explicit_config2(dev):
     fs = host.factorize_problem(prob.subdomains)
     lam = np.random.default_rng(3).standard_normal(prob.n_dual)
     ip, qi = _implicit_q(fs, prob.n_dual, lam, dev)
+    _, qs = _implicit_q(fs, prob.n_dual, lam, dev, pairs=-1)     # one CTA per subdomain
     plan = sc.Plan(fs, prob.n_dual).upload(dev)
     Lv = torch.from_numpy(sc.concat_L_values(fs)).to(dev)
     F = plan.new_F(dev)
@@ -118,8 +123,9 @@ def test_implicit_equals_explicit_config2(dev):
     qo = oracle.apply_dual(oracle.dual_operators(prob.subdomains, memo, refine=1),
                            [s.lambda_map for s in prob.subdomains], lam, prob.n_dual)
     e_imp, e_exp, e_ie = _rel(qi, qo), _rel(qe, qo), _rel(qi, qe)
-    print(f"config 2: implicit {e_imp:.3e}, explicit {e_exp:.3e}, implicit vs explicit {e_ie:.3e}")
-    assert e_imp <= TOL and e_exp <= TOL and e_ie <= TOL
+    print(f"config 2: implicit {e_imp:.3e}, explicit {e_exp:.3e}, implicit vs explicit {e_ie:.3e}, "
+          f"CTA pairs vs one CTA {_rel(qi, qs):.3e}")
+    assert e_imp <= TOL and e_exp <= TOL and e_ie <= TOL and _rel(qi, qs) <= TOL
 
 
 def test_implicit_repeatable_and_reusable(dev):
