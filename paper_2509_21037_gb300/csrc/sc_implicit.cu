@@ -49,11 +49,11 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-// 16 warps per CTA and one CTA per SM: a subdomain that a CTA solves alone
-// gets twice the warps for the wide lower levels of its elimination tree
-// (many small supernodes, one warp each), where the solve spends most of
-// its time when there are fewer subdomains than SMs
-constexpr int kWarps = 16;
+// 16 warps per CTA and one CTA per SM while a batch has at most one
+// subdomain per SM: a subdomain that a CTA solves alone gets twice the warps
+// for the wide lower levels of its elimination tree (many small supernodes,
+// one warp each); 8 warps and two CTAs per SM for larger batches
+constexpr int kWarps = 16;      // warps per CTA at most (the planner picks 8 or 16 per batch)
 constexpr int kCluster = 8;     // CTAs per cluster (portable maximum)
 constexpr int64_t kCtaSlots = 152;   // resident CTAs on a GB300 (152 SMs, 1 CTA each)
 constexpr int kThreadsI = 32 * kWarps;
@@ -122,8 +122,9 @@ struct IPtrs {
   int64_t rd_off;      // doubles from a subdomain's x to its reciprocal diagonals (workspace)
 };
 
-__device__ __forceinline__ int64_t col_off(int t, int nr) {
-  return (int64_t)t * nr - (int64_t)t * (t - 1) / 2;
+__device__ __forceinline__ int col_off(int t, int nr) {
+  // 32-bit: the planner checks that every visited panel holds fewer than 2^31 entries
+  return t * nr - t * (t - 1) / 2;
 }
 
 // Loads of x: when a subdomain spans a cluster, x is written by several SMs
@@ -139,17 +140,15 @@ __device__ __forceinline__ double ldx(const double *p) {
 template <bool CL>
 __device__ __forceinline__ double forward_triangle(const double *__restrict__ L, int nr, int kb, int w, double *xs,
                                                    int64_t rd_off, int lane) {
-  const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
   const double inv = lane < w ? ldx<CL>(xs + rd_off + kb + lane) : 0.0;   // 1 / L(c, c), computed per call
-  // lane i: L(kb + i, kb + k) for k < i, entry (i - k) of column kb + k
+  // lane i: L(kb + i, kb + k) for k < i, entry (i - k) of column kb + k, at
+  // col_off(kb + k) + i - k: one offset stepped by nr - (kb + k) - 1 per column
   double lv[32];
+  int o = col_off(kb, nr) + lane;
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
-    lv[k] = 0.0;
-    if (k < w) {
-      const int64_t ck = __shfl_sync(kFull, coff, k);
-      if (k < lane && lane < w) lv[k] = L[ck + (lane - k)];
-    }
+    lv[k] = (k < w && k < lane && lane < w) ? L[o] : 0.0;
+    o += nr - (kb + k) - 1;
   }
   double xi = lane < w ? ldx<CL>(xs + kb + lane) : 0.0;
 #pragma unroll
@@ -175,7 +174,13 @@ __device__ __forceinline__ void forward_panel_chunk(const double *__restrict__ L
   const bool ok = t < nr;
   double lv[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) lv[k] = (k < w && ok) ? L[col_off(kb + k, nr) + (t - kb - k)] : 0.0;
+  // entry (t, c) of the panel at col_off(c) + t - c, and col_off(c + 1) = col_off(c) + nr - c
+  int o = col_off(kb, nr) + (t - kb);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    lv[k] = (k < w && ok) ? L[o] : 0.0;
+    o += nr - (kb + k) - 1;
+  }
   double acc = 0.0;
 #pragma unroll
   for (int k = 0; k < 32; ++k)
@@ -193,9 +198,12 @@ __device__ __forceinline__ void backward_panel_chunk(const double *__restrict__ 
   const int t = t0 + lane;
   const bool ok = t < nr;
   const double zt = ok ? (t < ns ? ldx<CL>(xs + t) : ldx<CL>(x + R[t - ns])) : 0.0;
+  int o = col_off(kb, nr) + (t - kb);
 #pragma unroll
-  for (int k = 0; k < 32; ++k)
-    if (k < w && ok) acc[k] = fma(L[col_off(kb + k, nr) + (t - kb - k)], zt, acc[k]);
+  for (int k = 0; k < 32; ++k) {
+    if (k < w && ok) acc[k] = fma(L[o], zt, acc[k]);
+    o += nr - (kb + k) - 1;
+  }
 }
 
 // Warp transpose-reduce: on return lane k holds the sum over the warp's lanes
@@ -241,12 +249,12 @@ __device__ __forceinline__ double transpose_reduce_w(double (&acc)[32], int lane
 template <bool CL>
 __device__ __forceinline__ void backward_triangle(const double *__restrict__ L, int nr, int kb, int w, double rhs,
                                                   double *xs, int64_t rd_off, int lane) {
-  const int64_t coff = lane < w ? col_off(kb + lane, nr) : 0;
   const double inv = lane < w ? ldx<CL>(xs + rd_off + kb + lane) : 0.0;
   // lane k: L(kb + i, kb + k) for i > k, entry (i - k) of its own column
+  const double *pc = L + (lane < w ? col_off(kb + lane, nr) - lane : 0);
   double lc[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) lc[i] = (i > lane && i < w) ? L[coff + (i - lane)] : 0.0;
+  for (int i = 0; i < 32; ++i) lc[i] = (i > lane && i < w) ? pc[i] : 0.0;
 #pragma unroll
   for (int i = 31; i >= 0; --i) {
     if (i < w) {   // uniform
@@ -278,19 +286,21 @@ struct Group {
   }
 };
 
+__device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
+
 __device__ __forceinline__ Group cta_group(int warp, int lane) {
-  return Group{0, 1, warp, lane, warp, kWarps, false, 0, kWarps, 0, 0};
+  return Group{0, 1, warp, lane, warp, nwarps(), false, 0, nwarps(), 0, 0};
 }
 
 // warps [w0, w0 + nwl) of this CTA, named barrier 1 + slot (slot < kWarps - 1)
 __device__ __forceinline__ Group sub_group(int warp, int lane, int w0, int nwl, int slot) {
-  return Group{0, 1, warp, lane, warp - w0, nwl, false, w0, nwl, nwl == kWarps ? 0 : 1 + slot, slot};
+  return Group{0, 1, warp, lane, warp - w0, nwl, false, w0, nwl, nwl == nwarps() ? 0 : 1 + slot, slot};
 }
 
 __device__ __forceinline__ Group cluster_group(int warp, int lane) {
   cg::cluster_group c = cg::this_cluster();
   const int r = (int)c.block_rank(), n = (int)c.num_blocks();
-  return Group{r, n, warp, lane, r * kWarps + warp, n * kWarps, true, 0, kWarps, 0, 0};
+  return Group{r, n, warp, lane, r * nwarps() + warp, n * nwarps(), true, 0, nwarps(), 0, 0};
 }
 
 // One supernode by one warp.
@@ -434,8 +444,8 @@ __device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n
       g.sync();
     } else if (!g.cluster && b - a >= 2) {
       // 2 .. 7 supernodes on one CTA: each on its own subgroup of the warps, side by side
-      const int c = b - a, j = g.warp * c / kWarps, w0 = (kWarps * j + c - 1) / c;
-      const Group sg = sub_group(g.warp, g.lane, w0, (kWarps * (j + 1) + c - 1) / c - w0, j);
+      const int W = nwarps(), c = b - a, j = g.warp * c / W, w0 = (W * j + c - 1) / c;
+      const Group sg = sub_group(g.warp, g.lane, w0, (W * (j + 1) + c - 1) / c - w0, j);
       forward_group<CL>(sg, P.sns[a + j], Lv, P.rows, x, ys[g.warp], rd);
       __syncthreads();
     } else if (b - a >= g.size) {
@@ -459,8 +469,8 @@ __device__ void backward_levels(const Group &g, const IPtrs &P, int lev_lo, int 
       for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, rd, g.lane);
       g.sync();
     } else if (!g.cluster && b - a >= 2) {
-      const int c = b - a, j = g.warp * c / kWarps, w0 = (kWarps * j + c - 1) / c;
-      const Group sg = sub_group(g.warp, g.lane, w0, (kWarps * (j + 1) + c - 1) / c - w0, j);
+      const int W = nwarps(), c = b - a, j = g.warp * c / W, w0 = (W * j + c - 1) / c;
+      const Group sg = sub_group(g.warp, g.lane, w0, (W * (j + 1) + c - 1) / c - w0, j);
       backward_group<CL>(sg, P.sns[a + j], Lv, P.rows, x, rd, red, red_cta);
       __syncthreads();
     } else if (b - a >= g.size) {
@@ -535,7 +545,7 @@ __device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, 
                                 const double *__restrict__ lam, double *q, double *X, uint32_t *status,
                                 double (*ys)[32], double *red, double *red_cta) {
   const int tid = g.warp * 32 + g.lane;
-  const int gt = g.rank * kThreadsI + tid, nt = g.size * kThreadsI;
+  const int gt = g.rank * (int)blockDim.x + tid, nt = g.size * (int)blockDim.x;
   double *x = X + sd.x_off;
   gather_x(P, sd, Lv, lam, x, gt, nt, g, status);
   g.sync();
@@ -571,20 +581,20 @@ __device__ void solve_pair_item(const IItem &it, const IPtrs &P, const double *_
   const int lev_part = part == 0 ? sd.lev_lo : sd.lev_lo + sd.n_lev_a;
   const int n_part = part == 0 ? sd.n_lev_a : sd.n_lev_b;
   const int lev_top = sd.lev_lo + sd.n_lev_a + sd.n_lev_b, n_top = sd.n_lev - sd.n_lev_a - sd.n_lev_b;
-  if (act && part == 0) gather_x(P, sd, Lv, lam, x, tid, kThreadsI, cta, status);
+  if (act && part == 0) gather_x(P, sd, Lv, lam, x, tid, (int)blockDim.x, cta, status);
   cl.sync();                                                             // S1
   if (act) forward_levels<false>(cta, P, lev_part, n_part, Lv, x, ys);
   cl.sync();                                                             // S2
   if (act && part == 0) {
     forward_levels<true>(cta, P, lev_top, n_top, Lv, x, ys);
     backward_levels<true>(cta, P, lev_top, n_top, Lv, x, red, red_cta);
-    scatter_q<true>(P, sd.s_mid2, sd.s_hi, x, q, tid, kThreadsI);
+    scatter_q<true>(P, sd.s_mid2, sd.s_hi, x, q, tid, (int)blockDim.x);
   }
   cl.sync();                                                             // S3
   if (act) {
     backward_levels<true>(cta, P, lev_part, n_part, Lv, x, red, red_cta);
-    if (part == 0) scatter_q<true>(P, sd.s_lo, sd.s_mid1, x, q, tid, kThreadsI);
-    else scatter_q<true>(P, sd.s_mid1, sd.s_mid2, x, q, tid, kThreadsI);
+    if (part == 0) scatter_q<true>(P, sd.s_lo, sd.s_mid1, x, q, tid, (int)blockDim.x);
+    else scatter_q<true>(P, sd.s_mid1, sd.s_mid2, x, q, tid, (int)blockDim.x);
   }
 }
 
@@ -628,6 +638,7 @@ struct sci_ctx {
   int64_t n_items = 0;
   int64_t n_pair_subdomains = 0;    // subdomains on CTA pairs (the launch then needs clusters)
   int64_t x_total = 0;              // doubles of all subdomains' x (the reciprocal diagonals follow)
+  int32_t warps = kWarps;           // warps per CTA of the launch
 
   IPtrs ptrs() const {
     const uint8_t *b = static_cast<const uint8_t *>(plan_dev);
@@ -785,6 +796,10 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
       }
       ISn sn{};
       const int32_t c0 = S.sn_c0[s], ns = S.sn_ns[s], rs = S.sn_rs[s];
+      // the kernel addresses a panel with 32-bit offsets
+      if ((int64_t)ns * (ns + rs) - (int64_t)ns * (ns - 1) / 2 >= (int64_t(1) << 31))
+        return ifail(ctx, SC_ERR_INVALID_ARG, "subdomain " + std::to_string(i) +
+                                                  ": a supernode panel of 2^31 or more entries (sci_plan addresses panels in 32 bits)");
       sn.lval = L_off[i] + D.L_colptr[c0];
       sn.rows_off = (int64_t)rows.size();
       sn.c0 = c0;
@@ -864,6 +879,11 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
     items.push_back(it);
   }
   ctx->n_items = (int64_t)items.size();
+  // 16 warps and one CTA per SM while the batch has at most one subdomain per
+  // SM (a subdomain alone on its SM gets twice the warps for its wide lower
+  // levels); 8 warps and two CTAs per SM beyond, so that twice as many
+  // subdomains run at once
+  ctx->warps = nsub <= kCtaSlots ? kWarps : kWarps / 2;
   int64_t n_big = 0;
   ctx->n_pair_subdomains = 0;
   for (const IItem &it : items) {
@@ -971,7 +991,7 @@ sc_status sci_apply(sci_ctx *ctx, const double *L_values_dev, const double *lamb
   if (e == cudaSuccess && ctx->n_items > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ctx->n_items * kCluster));
-    cfg.blockDim = dim3(kThreadsI);
+    cfg.blockDim = dim3(32 * ctx->warps);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

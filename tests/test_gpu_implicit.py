@@ -167,3 +167,16 @@ def test_implicit_workspace_checks(dev):
     q = torch.empty(prob.n_dual, dtype=torch.float64, device=dev)
     with pytest.raises(sc.SCError, match="SC_ERR_OOM"):
         ip.apply(Lv, torch.ones(prob.n_dual, dtype=torch.float64, device=dev), q)
+
+
+def test_implicit_large_batch_two_ctas_per_sm(dev):
+    """More subdomains than SMs (176 on 152): the launch takes 8 warps and two
+    CTAs per SM; q still matches the oracle."""
+    prob = synth.mixed_batch(lat2d=(14, 12), k2d=(4, 10), lat3d=(2, 2, 2), k3d=(2, 4), seed=5)
+    assert len(prob.subdomains) > 152
+    fs = host.factorize_problem(prob.subdomains)
+    lam = np.random.default_rng(8).standard_normal(prob.n_dual)
+    _, q = _implicit_q(fs, prob.n_dual, lam, dev)
+    err = _rel(q, _oracle_q(prob.subdomains, lam, prob.n_dual, refine=1))
+    print(f"{len(fs)} subdomains: implicit apply vs oracle {err:.3e}")
+    assert err <= TOL
