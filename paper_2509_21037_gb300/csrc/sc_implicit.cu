@@ -430,9 +430,21 @@ __device__ void prefetch_level(const Group &g, const IPtrs &P, int lev, const do
 // CTA per supernode (the CTA's warps share its panel rows); else (the top
 // separators) one supernode at a time on the whole group.  One group barrier
 // per level, two per 32-column block in the last case.
+// ctr (one CTA's group only; nullptr for a cluster): a shared counter from
+// which the warps of a level with one warp per supernode take their next
+// supernode (largest first, as the planner orders them), so that they finish
+// the level together; never reset within a call -- `base` counts the takes so
+// far (a level of c supernodes takes c + (warps) times: each warp's last take
+// finds the level empty).
+__device__ __forceinline__ int take(int *ctr, int base, int lane) {
+  int idx = 0;
+  if (lane == 0) idx = atomicAdd(ctr, 1) - base;
+  return __shfl_sync(kFull, idx, 0);
+}
+
 template <bool CL>
 __device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n_lev, const double *__restrict__ Lv,
-                               double *x, double (*ys)[32]) {
+                               double *x, double (*ys)[32], int *ctr, int &base) {
   const int64_t rd = P.rd_off;
   const Group cta = cta_group(g.warp, g.lane);
   if (n_lev > 0) prefetch_level(g, P, lev_lo, Lv);
@@ -440,7 +452,13 @@ __device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n
     if (l + 1 < n_lev) prefetch_level(g, P, lev_lo + l + 1, Lv);
     const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
     if (2 * (b - a) >= g.nw) {
-      for (int s = a + g.gw; s < b; s += g.nw) forward_warp<CL>(P.sns[s], Lv, P.rows, x, ys[g.warp], rd, g.lane);
+      if (ctr) {
+        for (int k = take(ctr, base, g.lane); k < b - a; k = take(ctr, base, g.lane))
+          forward_warp<CL>(P.sns[a + k], Lv, P.rows, x, ys[g.warp], rd, g.lane);
+        base += (b - a) + g.nw;
+      } else {
+        for (int s = a + g.gw; s < b; s += g.nw) forward_warp<CL>(P.sns[s], Lv, P.rows, x, ys[g.warp], rd, g.lane);
+      }
       g.sync();
     } else if (!g.cluster && b - a >= 2) {
       // 2 .. 7 supernodes on one CTA: each on its own subgroup of the warps, side by side
@@ -459,14 +477,21 @@ __device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n
 
 template <bool CL>
 __device__ void backward_levels(const Group &g, const IPtrs &P, int lev_lo, int n_lev,
-                                const double *__restrict__ Lv, double *x, double *red, double *red_cta) {
+                                const double *__restrict__ Lv, double *x, double *red, double *red_cta, int *ctr,
+                                int &base) {
   const int64_t rd = P.rd_off;
   const Group cta = cta_group(g.warp, g.lane);
   for (int l = n_lev - 1; l >= 0; --l) {
     if (l > 0) prefetch_level(g, P, lev_lo + l - 1, Lv);
     const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
     if (2 * (b - a) >= g.nw) {
-      for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, rd, g.lane);
+      if (ctr) {
+        for (int k = take(ctr, base, g.lane); k < b - a; k = take(ctr, base, g.lane))
+          backward_warp<CL>(P.sns[a + k], Lv, P.rows, x, rd, g.lane);
+        base += (b - a) + g.nw;
+      } else {
+        for (int s = a + g.gw; s < b; s += g.nw) backward_warp<CL>(P.sns[s], Lv, P.rows, x, rd, g.lane);
+      }
       g.sync();
     } else if (!g.cluster && b - a >= 2) {
       const int W = nwarps(), c = b - a, j = g.warp * c / W, w0 = (W * j + c - 1) / c;
@@ -543,14 +568,15 @@ __device__ void scatter_q(const IPtrs &P, int e_lo, int e_hi, const double *x, d
 template <bool CL>
 __device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, const double *__restrict__ Lv,
                                 const double *__restrict__ lam, double *q, double *X, uint32_t *status,
-                                double (*ys)[32], double *red, double *red_cta) {
+                                double (*ys)[32], double *red, double *red_cta, int *ctr) {
   const int tid = g.warp * 32 + g.lane;
   const int gt = g.rank * (int)blockDim.x + tid, nt = g.size * (int)blockDim.x;
   double *x = X + sd.x_off;
   gather_x(P, sd, Lv, lam, x, gt, nt, g, status);
   g.sync();
-  forward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, ys);
-  backward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, red, red_cta);
+  int base = 0;
+  forward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, ys, ctr, base);
+  backward_levels<CL>(g, P, sd.lev_lo, sd.n_lev, Lv, x, red, red_cta, ctr, base);
   scatter_q<CL>(P, sd.s_lo, sd.s_hi, x, q, gt, nt);
 }
 
@@ -569,7 +595,7 @@ __device__ void solve_subdomain(const Group &g, const IPtrs &P, const ISub &sd, 
 // rows that it or its own warps wrote, or that were complete at a barrier.
 __device__ void solve_pair_item(const IItem &it, const IPtrs &P, const double *__restrict__ Lv,
                                 const double *__restrict__ lam, double *q, double *X, uint32_t *status,
-                                double (*ys)[32], double *red, double *red_cta, int warp, int lane) {
+                                double (*ys)[32], double *red, double *red_cta, int *ctr, int warp, int lane) {
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank(), j = r >> 1, part = r & 1;
   const bool act = j < it.n;
@@ -583,16 +609,17 @@ __device__ void solve_pair_item(const IItem &it, const IPtrs &P, const double *_
   const int lev_top = sd.lev_lo + sd.n_lev_a + sd.n_lev_b, n_top = sd.n_lev - sd.n_lev_a - sd.n_lev_b;
   if (act && part == 0) gather_x(P, sd, Lv, lam, x, tid, (int)blockDim.x, cta, status);
   cl.sync();                                                             // S1
-  if (act) forward_levels<false>(cta, P, lev_part, n_part, Lv, x, ys);
+  int base = 0;
+  if (act) forward_levels<false>(cta, P, lev_part, n_part, Lv, x, ys, ctr, base);
   cl.sync();                                                             // S2
   if (act && part == 0) {
-    forward_levels<true>(cta, P, lev_top, n_top, Lv, x, ys);
-    backward_levels<true>(cta, P, lev_top, n_top, Lv, x, red, red_cta);
+    forward_levels<true>(cta, P, lev_top, n_top, Lv, x, ys, ctr, base);
+    backward_levels<true>(cta, P, lev_top, n_top, Lv, x, red, red_cta, ctr, base);
     scatter_q<true>(P, sd.s_mid2, sd.s_hi, x, q, tid, (int)blockDim.x);
   }
   cl.sync();                                                             // S3
   if (act) {
-    backward_levels<true>(cta, P, lev_part, n_part, Lv, x, red, red_cta);
+    backward_levels<true>(cta, P, lev_part, n_part, Lv, x, red, red_cta, ctr, base);
     if (part == 0) scatter_q<true>(P, sd.s_lo, sd.s_mid1, x, q, tid, (int)blockDim.x);
     else scatter_q<true>(P, sd.s_mid1, sd.s_mid2, x, q, tid, (int)blockDim.x);
   }
@@ -607,19 +634,21 @@ __global__ void __launch_bounds__(kThreadsI, 1) implicit_kernel(const IPtrs P, c
   __shared__ double ys[kWarps][32];
   __shared__ double red[kWarps * 32];
   __shared__ double red_cta[kWarps * 32];          // one 32-double row per (sub)group
+  __shared__ int take_ctr;                          // supernodes taken (see take); zero before the first barrier
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) take_ctr = 0;
   const IItem it = P.items[blockIdx.x / kCluster];
   if (it.kind == 0) {
     const Group g = cluster_group(warp, lane);
-    solve_subdomain<true>(g, P, P.subs[it.sub[0]], Lv, lam, q, X, status, ys, red, red_cta);
+    solve_subdomain<true>(g, P, P.subs[it.sub[0]], Lv, lam, q, X, status, ys, red, red_cta, nullptr);
     cg::this_cluster().sync();   // no CTA leaves while the first one may read its shared memory
   } else if (it.kind == 2) {
-    solve_pair_item(it, P, Lv, lam, q, X, status, ys, red, red_cta, warp, lane);
+    solve_pair_item(it, P, Lv, lam, q, X, status, ys, red, red_cta, &take_ctr, warp, lane);
   } else {
     const int r = (int)(blockIdx.x % kCluster);   // also without a cluster launch
     if (r < it.n) {
       const Group g = cta_group(warp, lane);
-      solve_subdomain<false>(g, P, P.subs[it.sub[r]], Lv, lam, q, X, status, ys, red, red_cta);
+      solve_subdomain<false>(g, P, P.subs[it.sub[r]], Lv, lam, q, X, status, ys, red, red_cta, &take_ctr);
     }
   }
 }
@@ -776,9 +805,14 @@ sc_status build(sci_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d, int64_t 
     const bool pair = want_pairs && work[i] < cluster_min_work && split_tree(S, vis, part);
     if (!pair) part.assign(nsn, 2);
     is_pair[i] = pair;
-    // (part, level, first column): parts A, B, then the top; one level sequence each
+    // (part, level, work descending): parts A, B, then the top, one level
+    // sequence each; within a level the largest supernodes first, so that the
+    // warps taking them in turn finish the level together
+    auto snw = [&](int32_t s) { return (int64_t)S.sn_ns[s] * (S.sn_ns[s] + 1) / 2 + (int64_t)S.sn_ns[s] * S.sn_rs[s]; };
     std::stable_sort(vis.begin(), vis.end(), [&](int32_t a, int32_t b) {
-      return part[a] != part[b] ? part[a] < part[b] : h[a] < h[b];
+      if (part[a] != part[b]) return part[a] < part[b];
+      if (h[a] != h[b]) return h[a] < h[b];
+      return snw(a) > snw(b);
     });
     ISub sd{};
     sd.x_off = x_off[i];
