@@ -340,6 +340,122 @@ __device__ void backward_warp(const ISn &sn, const double *__restrict__ Lv, cons
   }
 }
 
+// Two supernodes of at most 16 columns on one warp, one per 16-lane half
+// (lane & 15 = row or column within the half).  Every loop runs to the
+// larger of the two halves' bounds and every shuffle and __syncwarp is taken
+// by the whole warp; a half's rows and columns past its own supernode stay
+// zero, so they add nothing.  valid = false: the half has no supernode.  A
+// supernode of at most 16 columns is one block, and every row below it is a
+// pruned row (an ancestor's).
+template <bool CL>
+__device__ void forward_half(const ISn &sn, bool valid, const double *__restrict__ Lv,
+                             const int32_t *__restrict__ rows, double *x, double *ys, int64_t rd_off, int lane) {
+  const int hl = lane & 15, h = lane >> 4;
+  const int ns = valid ? sn.ns : 0, nr = valid ? sn.ns + sn.rs : 0;
+  const double *L = Lv + (valid ? sn.lval : 0);
+  const int32_t *R = rows + (valid ? sn.rows_off : 0);
+  double *xs = x + (valid ? sn.c0 : 0);
+  const int wmax = max(ns, __shfl_xor_sync(kFull, ns, 16));
+  const int nch = (nr - ns + 15) >> 4, chmax = max(nch, __shfl_xor_sync(kFull, nch, 16));
+  const double inv = hl < ns ? ldx<CL>(xs + rd_off + hl) : 0.0;
+  // lane i: L(i, k) for k < i, entry (i - k) of column k (offsets stepped column to column)
+  double lv[16];
+  int o = hl;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    lv[k] = (k < ns && k < hl && hl < ns) ? L[o] : 0.0;
+    o += nr - k - 1;
+  }
+  double xi = hl < ns ? ldx<CL>(xs + hl) : 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k < wmax) {   // uniform
+      const double yk = __shfl_sync(kFull, xi, k, 16) * __shfl_sync(kFull, inv, k, 16);
+      xi = hl == k ? yk : fma(-lv[k], yk, xi);
+    }
+  }
+  if (hl < ns) xs[hl] = xi;
+  ys[16 * h + hl] = hl < ns ? xi : 0.0;
+  __syncwarp();
+  for (int ch = 0; ch < chmax; ++ch) {
+    const int t = ns + 16 * ch + hl;
+    const bool ok = t < nr;
+    int oo = t;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < wmax) {   // uniform
+        const double l = (k < ns && ok) ? L[oo] : 0.0;
+        acc = fma(l, ys[16 * h + k], acc);
+      }
+      oo += nr - k - 1;
+    }
+    if (ok) atomicAdd(x + R[t - ns], -acc);
+  }
+  __syncwarp();
+}
+
+template <bool CL>
+__device__ void backward_half(const ISn &sn, bool valid, const double *__restrict__ Lv,
+                              const int32_t *__restrict__ rows, double *x, int64_t rd_off, int lane) {
+  const int hl = lane & 15;
+  const int ns = valid ? sn.ns : 0, nr = valid ? sn.ns + sn.rs : 0;
+  const double *L = Lv + (valid ? sn.lval : 0);
+  const int32_t *R = rows + (valid ? sn.rows_off : 0);
+  double *xs = x + (valid ? sn.c0 : 0);
+  const int wmax = max(ns, __shfl_xor_sync(kFull, ns, 16));
+  const int nch = (nr - ns + 15) >> 4, chmax = max(nch, __shfl_xor_sync(kFull, nch, 16));
+  double acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+  for (int ch = 0; ch < chmax; ++ch) {
+    const int t = ns + 16 * ch + hl;
+    const bool ok = t < nr;
+    const double zt = ok ? ldx<CL>(x + R[t - ns]) : 0.0;
+    int oo = t;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < wmax && k < ns && ok) acc[k] = fma(L[oo], zt, acc[k]);
+      oo += nr - k - 1;
+    }
+  }
+  // sum of acc[k] over the half's lanes, lane k of the half ending with column k: a
+  // transpose-reduce over groups of P lanes (P the power of two >= wmax), then a butterfly
+  // across the half's 16 / P groups (xor distances below 16 stay inside the half)
+  const int P = wmax <= 1 ? 1 : wmax <= 2 ? 2 : wmax <= 4 ? 4 : wmax <= 8 ? 8 : 16;
+#pragma unroll
+  for (int hh = 8; hh >= 1; hh >>= 1) {
+    if (hh < P) {   // uniform
+      const bool up = (lane & hh) != 0;
+#pragma unroll
+      for (int j = 0; j < hh; ++j) {
+        const double send = up ? acc[j] : acc[j + hh];
+        const double keep = up ? acc[j + hh] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(kFull, send, hh);
+      }
+    }
+  }
+  double part = acc[0];
+  for (int m = P; m < 16; m <<= 1) part += __shfl_xor_sync(kFull, part, m);
+  double rhs = hl < ns ? ldx<CL>(xs + hl) - part : 0.0;
+  const double inv = hl < ns ? ldx<CL>(xs + rd_off + hl) : 0.0;
+  // lane k: L(i, k) for i > k, entry (i - k) of its own column
+  const double *pc = L + (hl < ns ? col_off(hl, nr) - hl : 0);
+  double lc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) lc[i] = (i > hl && i < ns) ? pc[i] : 0.0;
+#pragma unroll
+  for (int i = 15; i >= 0; --i) {
+    if (i < wmax) {   // uniform
+      if (hl == i) rhs *= inv;
+      const double zi = __shfl_sync(kFull, rhs, i, 16);
+      rhs = fma(-lc[i], zi, rhs);
+    }
+  }
+  if (hl < ns) xs[hl] = rhs;
+  __syncwarp();
+}
+
 // One supernode by a CTA (CL = false; warps of this CTA) or by the whole
 // cluster (CL = true): the triangle by the group's first warp, the panel rows
 // spread over all the group's warps.
@@ -436,10 +552,38 @@ __device__ void prefetch_level(const Group &g, const IPtrs &P, int lev, const do
 // the level together; never reset within a call -- `base` counts the takes so
 // far (a level of c supernodes takes c + (warps) times: each warp's last take
 // finds the level empty).
-__device__ __forceinline__ int take(int *ctr, int base, int lane) {
+__device__ __forceinline__ int take(int *ctr, int base, int lane, int n = 1) {
   int idx = 0;
-  if (lane == 0) idx = atomicAdd(ctr, 1) - base;
+  if (lane == 0) idx = atomicAdd(ctr, n) - base;
   return __shfl_sync(kFull, idx, 0);
+}
+
+// A level whose largest supernode (the first: the planner orders a level by
+// work) has at most 16 columns is taken two supernodes at a time, one per
+// half-warp (forward_half / backward_half); a pair with a wider member runs
+// on the whole warp one after the other.  The level then takes
+// 2 (ceil(c / 2) + warps) numbers.
+template <bool CL, bool FWD>
+__device__ void tiny_level(const Group &g, const IPtrs &P, int a, int c, const double *__restrict__ Lv, double *x,
+                           double *ys, int64_t rd, int *ctr, int &base) {
+  for (int k = take(ctr, base, g.lane, 2); k < c; k = take(ctr, base, g.lane, 2)) {
+    const ISn s0 = P.sns[a + k];
+    const bool two = k + 1 < c;
+    const ISn s1 = two ? P.sns[a + k + 1] : s0;
+    if (s0.ns <= 16 && (!two || s1.ns <= 16)) {
+      const bool hi = g.lane >= 16;
+      if (FWD) forward_half<CL>(hi ? s1 : s0, !hi || two, Lv, P.rows, x, ys, rd, g.lane);
+      else backward_half<CL>(hi ? s1 : s0, !hi || two, Lv, P.rows, x, rd, g.lane);
+    } else {
+      if (FWD) forward_warp<CL>(s0, Lv, P.rows, x, ys, rd, g.lane);
+      else backward_warp<CL>(s0, Lv, P.rows, x, rd, g.lane);
+      if (two) {
+        if (FWD) forward_warp<CL>(s1, Lv, P.rows, x, ys, rd, g.lane);
+        else backward_warp<CL>(s1, Lv, P.rows, x, rd, g.lane);
+      }
+    }
+  }
+  base += 2 * ((c + 1) / 2 + g.nw);
 }
 
 template <bool CL>
@@ -452,7 +596,9 @@ __device__ void forward_levels(const Group &g, const IPtrs &P, int lev_lo, int n
     if (l + 1 < n_lev) prefetch_level(g, P, lev_lo + l + 1, Lv);
     const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
     if (2 * (b - a) >= g.nw) {
-      if (ctr) {
+      if (ctr && P.sns[a].ns <= 16) {
+        tiny_level<CL, true>(g, P, a, b - a, Lv, x, ys[g.warp], rd, ctr, base);
+      } else if (ctr) {
         for (int k = take(ctr, base, g.lane); k < b - a; k = take(ctr, base, g.lane))
           forward_warp<CL>(P.sns[a + k], Lv, P.rows, x, ys[g.warp], rd, g.lane);
         base += (b - a) + g.nw;
@@ -485,7 +631,9 @@ __device__ void backward_levels(const Group &g, const IPtrs &P, int lev_lo, int 
     if (l > 0) prefetch_level(g, P, lev_lo + l - 1, Lv);
     const int a = P.levptr[lev_lo + l], b = P.levptr[lev_lo + l + 1];
     if (2 * (b - a) >= g.nw) {
-      if (ctr) {
+      if (ctr && P.sns[a].ns <= 16) {
+        tiny_level<CL, false>(g, P, a, b - a, Lv, x, nullptr, rd, ctr, base);
+      } else if (ctr) {
         for (int k = take(ctr, base, g.lane); k < b - a; k = take(ctr, base, g.lane))
           backward_warp<CL>(P.sns[a + k], Lv, P.rows, x, rd, g.lane);
         base += (b - a) + g.nw;
@@ -536,8 +684,23 @@ __device__ void gather_x(const IPtrs &P, const ISub &sd, const double *__restric
                          uint32_t *status) {
   for (int c = gt; c < sd.n; c += nt) x[c] = 0.0;
   double *rd = x + P.rd_off;
+  // one supernode per thread up to 32 columns (independent loads side by side), a warp per larger one
+  for (int s = sd.sn_lo + gt; s < sd.sn_hi; s += nt) {
+    const ISn sn = P.sns[s];
+    if (sn.ns > 32) continue;
+    const int nr = sn.ns + sn.rs;
+    int o = 0;
+    for (int t = 0; t < sn.ns; ++t) {
+      bool ok;
+      const double r = pos_recip(Lv[sn.lval + o], ok);
+      if (!ok) atomicOr(status, 1u);
+      rd[sn.c0 + t] = ok ? r : 0.0;
+      o += nr - t;
+    }
+  }
   for (int s = sd.sn_lo + gt / 32; s < sd.sn_hi; s += nt / 32) {
     const ISn sn = P.sns[s];
+    if (sn.ns <= 32) continue;
     const int nr = sn.ns + sn.rs;
     for (int t = gt & 31; t < sn.ns; t += 32) {
       bool ok;
