@@ -393,18 +393,42 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
       };
       const bool pre = warp != tri && warp * 16 < nb;
       if (pre) load_afr(warp);
-      if (warp == tri) {
-        if (lane < kw) cps[lane] = cp[kb + lane] - (kb + lane);
-        __syncwarp();
-        int em = 0;
-        if (lane < wk) {
-          for (int q = 0; q < kw; ++q) Xs[q][lane] = Ys[(int64_t)(kb + q) * ws + lane];
-          for (int q = 0; q < kw; ++q) {
+      // The FP64 triangle, 8 columns at a time: warp `tri` solves the 8x8
+      // diagonal piece, then all four warps update the block's rows below it
+      // (one warp alone would hold its sub-partition's FP64 unit for the whole
+      // chain of ~kw^2 / 2 instructions while the others wait).  Every entry
+      // gets its updates in the same column order as a column-by-column solve.
+      if (tid < kw) cps[tid] = cp[kb + tid] - (kb + tid);
+      for (int e = tid; e < kw * 32; e += kThreads) {
+        const int q = e >> 5, c = e & 31;
+        Xs[q][c] = c < wk ? Ys[(int64_t)(kb + q) * ws + c] : 0.0;
+      }
+      __syncthreads();
+      for (int p0 = 0; p0 < kw; p0 += 8) {
+        const int pe = min(p0 + 8, kw);
+        if (warp == tri && lane < wk) {
+          for (int q = p0; q < pe; ++q) {
             const double xq = Xs[q][lane] * id[kb + q];
             Xs[q][lane] = xq;
             const double *Lc = Lv + cps[q];
-            for (int r = q + 1; r < kw; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
+            for (int r = q + 1; r < pe; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
           }
+        }
+        __syncthreads();
+        if (pe < kw) {
+          if (lane < wk) {
+            for (int r = pe + ((warp - tri) & 3); r < kw; r += kThreads / 32) {
+              double xr = Xs[r][lane];
+              for (int q = p0; q < pe; ++q) xr = fma(-Lv[cps[q] + kb + r], Xs[q][lane], xr);
+              Xs[r][lane] = xr;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (warp == tri) {
+        int em = 0;
+        if (lane < wk) {
           for (int q = 0; q < kw; ++q) {
             Ys[(int64_t)(kb + q) * ws + lane] = Xs[q][lane];
             em = max(em, biased_exponent(Xs[q][lane]));
