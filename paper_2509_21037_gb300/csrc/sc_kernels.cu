@@ -111,20 +111,39 @@ __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, c
       // columns at or after the block's cut are still zero in these rows
       const int wk = min(b, P.cuts[s.cut_off + (kb >> 5)]) - a;
       if (wk <= 0) continue;
-      if (warp == tri) {
-        if (lane < kw) cps[lane] = cp[kb + lane] - (kb + lane);
-        __syncwarp();
-        if (lane < wk) {
-          for (int q = 0; q < kw; ++q) Xs[q][lane] = Ys[(int64_t)(kb + q) * ws + lane];
-          for (int q = 0; q < kw; ++q) {
+      // The triangle, 8 columns at a time: warp `tri` solves the 8x8 diagonal
+      // piece, then all warps update the block's rows below it (every entry
+      // gets its updates in the same column order as a column-by-column solve)
+      if (tid < kw) cps[tid] = cp[kb + tid] - (kb + tid);
+      for (int e = tid; e < kw * 32; e += kThreads) {
+        const int q = e >> 5, c = e & 31;
+        if (c < wk) Xs[q][c] = Ys[(int64_t)(kb + q) * ws + c];
+      }
+      __syncthreads();
+      for (int p0 = 0; p0 < kw; p0 += 8) {
+        const int pe = min(p0 + 8, kw);
+        if (warp == tri && lane < wk) {
+          for (int q = p0; q < pe; ++q) {
             const double xq = Xs[q][lane] * id[kb + q];
             Xs[q][lane] = xq;
             const double *Lc = Lv + cps[q];
-            for (int r = q + 1; r < kw; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
+            for (int r = q + 1; r < pe; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
           }
-          for (int q = 0; q < kw; ++q) Ys[(int64_t)(kb + q) * ws + lane] = Xs[q][lane];
+        }
+        __syncthreads();
+        if (pe < kw) {
+          if (lane < wk) {
+            for (int r = pe + ((warp - tri) & 3); r < kw; r += kThreads / 32) {
+              double xr = Xs[r][lane];
+              for (int q = p0; q < pe; ++q) xr = fma(-Lv[cps[q] + kb + r], Xs[q][lane], xr);
+              Xs[r][lane] = xr;
+            }
+          }
+          __syncthreads();
         }
       }
+      if (warp == tri && lane < wk)
+        for (int q = 0; q < kw; ++q) Ys[(int64_t)(kb + q) * ws + lane] = Xs[q][lane];
       __syncthreads();
       // Update of the rows below.  The FP64 pipe charges a warp instruction in
       // full whatever the number of active lanes, so the (row, column) pairs

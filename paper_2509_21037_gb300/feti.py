@@ -157,7 +157,8 @@ def dirichlet_problem(subdomains, threads: int = 0):
     restricted to the interior dofs, once per distinct (K_i, glued dofs) pair)
     and the general right-hand side C_i in its order (column j: s_j times the
     coupling column K_ib of multiplier j's dof; include/sc.h Bt_val) -- and
-    the dense first term B_b K_bb B_b^T in the local multiplier order."""
+    the sparse first term B_b K_bb B_b^T in the local multiplier order, as
+    its lower triangle (rows, cols, vals) with rows >= cols."""
     cache = {}
     todo = []
     keys = []
@@ -184,7 +185,7 @@ def dirichlet_problem(subdomains, threads: int = 0):
         order = pos[nd_cache[(tuple(sd.grid), sd.ndpn)]]
         order = order[order >= 0].astype(np.int32)
         L = host.factorize(K[inner][:, inner], [], order, postorder=True)
-        return key, (L, sp.csc_matrix(K[inner][:, b]), K[b][:, b].toarray())
+        return key, (L, sp.csc_matrix(K[inner][:, b]), sp.csr_matrix(K[b][:, b]))
 
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(max_workers=threads or None) as ex:
@@ -207,7 +208,10 @@ def dirichlet_problem(subdomains, threads: int = 0):
         ri, vals = rows[o], C.data[o]
         facs.append(host.FactoredSubdomain(L, cp, ri.astype(np.int32), np.ones(len(ri), np.int8),
                                            np.asarray(sd.lambda_map, np.int32), vals))
-        kbb.append(sg[:, None] * Kbb[np.ix_(pb, pb)] * sg[None, :])
+        S = sp.coo_matrix(Kbb[pb][:, pb])                      # entry (j, k) = K_bb[d_j, d_k]
+        low = S.row >= S.col
+        r, c = S.row[low], S.col[low]
+        kbb.append((r, c, S.data[low] * sg[r] * sg[c]))
     return facs, kbb
 
 
@@ -215,8 +219,8 @@ def dirichlet_operator_gpu(subdomains, plan, device, threads: int = 0):
     """sum_i B_i S_i B_i^T tile-packed in ``plan``'s F layout, its Schur
     complements assembled on the GPU by this library (``dirichlet_problem``:
     the interior factors and coupling columns, then sc_assemble_batch for
-    C_i^T K_ii^{-1} C_i, subtracted from the packed K_bb blocks).  Returns
-    (buffer, set-up seconds)."""
+    C_i^T K_ii^{-1} C_i, negated in place and the sparse K_bb entries added
+    to it).  Returns (buffer, set-up seconds)."""
     import torch
     t0 = time.perf_counter()
     facs, kbb = dirichlet_problem(subdomains, threads)
@@ -231,16 +235,13 @@ def dirichlet_operator_gpu(subdomains, plan, device, threads: int = 0):
         raise RuntimeError("F layouts differ")
     torch.cuda.synchronize(device)
     t3 = time.perf_counter()
-    M = plan.pack(kbb, device)
+    M = Fc.neg_()
+    plan.add_symmetric_batch(M, [(i, *e) for i, e in enumerate(kbb)])
     torch.cuda.synchronize(device)
     t4 = time.perf_counter()
-    M -= Fc
-    del Fc
-    torch.cuda.synchronize(device)
-    t5 = time.perf_counter()
     dirichlet_operator_gpu.last_breakdown = {"host_factors_and_coupling_s": t1 - t0, "plan_s": t2 - t1,
-                                             "assembly_s": t3 - t2, "pack_s": t4 - t3, "subtract_s": t5 - t4}
-    return M, t5 - t0
+                                             "assembly_s": t3 - t2, "kbb_add_s": t4 - t3}
+    return M, t4 - t0
 
 
 class _KPlus:

@@ -207,20 +207,28 @@ class Plan:
         """F_i[r, c] += v and F_i[c, r] += v (once for r == c) for entries
         with r >= c, in place in the tile-packed layout (the lower tile holds
         an off-diagonal-tile pair once; a diagonal tile stores both entries)."""
+        self.add_symmetric_batch(F, [(i, rows, cols, vals)])
+
+    def add_symmetric_batch(self, F, entries):
+        """``add_symmetric`` for several subdomains at once: entries is a
+        sequence of (i, rows, cols, vals); one scatter-add on F's device."""
         import torch
-        r = np.asarray(rows, np.int64)
-        c = np.asarray(cols, np.int64)
-        v = np.asarray(vals, np.float64)
-        assert np.all(r >= c) and len(r) == len(c) == len(v)
-        if len(r) == 0:
+        off, val = [], []
+        for i, rows, cols, vals in entries:
+            r = np.asarray(rows, np.int64)
+            c = np.asarray(cols, np.int64)
+            v = np.asarray(vals, np.float64)
+            assert np.all(r >= c) and len(r) == len(c) == len(v)
+            assert np.all(r < self.m[i]) and np.all(c >= 0)
+            I, J = r // 32, c // 32
+            base = int(self.F_offsets[i]) + (I * (I + 1) // 2 + J) * 1024
+            off.append(base + r % 32 + 32 * (c % 32))
+            val.append(v)
+            mirror = (I == J) & (r != c)             # a diagonal tile holds the mirror entry too
+            off.append(base[mirror] + c[mirror] % 32 + 32 * (r[mirror] % 32))
+            val.append(v[mirror])
+        if not off or sum(len(o) for o in off) == 0:
             return
-        I, J = r // 32, c // 32
-        base = int(self.F_offsets[i]) + (I * (I + 1) // 2 + J) * 1024
-        off = [base + r % 32 + 32 * (c % 32)]
-        val = [v]
-        mirror = (I == J) & (r != c)                 # a diagonal tile holds the mirror entry too
-        off.append(base[mirror] + c[mirror] % 32 + 32 * (r[mirror] % 32))
-        val.append(v[mirror])
         idx = torch.from_numpy(np.concatenate(off)).to(F.device)
         F.index_add_(0, idx, torch.from_numpy(np.concatenate(val)).to(F.device))
 

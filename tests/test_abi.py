@@ -648,3 +648,34 @@ def test_host_implicit_apply_rejects_bad_patterns(case):
         host.ImplicitApply(subs, prob.n_dual, planned=False)(x)
     with pytest.raises(RuntimeError):
         host.ImplicitApply(subs, prob.n_dual, planned=True)
+
+
+def test_add_symmetric_batch_matches_pack():
+    """Plan.add_symmetric_batch scatters lower-triangle entries (r >= c, with
+    repeats, which accumulate) of several subdomains into F's layout: on a
+    zero buffer it gives exactly the pack of the symmetric matrices they
+    define (an off-diagonal-tile pair stored once, a diagonal tile both
+    entries); the one-subdomain form agrees."""
+    torch = pytest.importorskip("torch")
+    prob = synth.cube_heat_3d(2, 3)
+    fs = host.factorize_problem(prob.subdomains)
+    plan = sc.Plan(fs, prob.n_dual)
+    rng = np.random.default_rng(12)
+    entries, mats = [], []
+    for i, m in enumerate(plan.m):
+        n = 4 * m
+        r, c = rng.integers(0, m, n), rng.integers(0, m, n)
+        r, c = np.maximum(r, c), np.minimum(r, c)
+        v = rng.integers(-8, 8, n).astype(np.float64)    # small integers: sums exact in any order
+        A = np.zeros((m, m))
+        np.add.at(A, (r, c), v)
+        mats.append(A + np.tril(A, -1).T)
+        entries.append((i, r, c, v))
+    want = plan.pack(mats, device="cpu")
+    got = torch.zeros_like(want)
+    plan.add_symmetric_batch(got, entries)
+    assert torch.equal(got, want)
+    one = torch.zeros_like(want)
+    for e in entries:
+        plan.add_symmetric(one, *e)
+    assert torch.equal(one, want)
