@@ -157,7 +157,7 @@ __device__ __forceinline__ void trsm_task(const PlanPtrs &P, const TrsmTask t, c
           // the target row is the accumulator: no separate subtraction on the FP64 pipe
           double *tg = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
           double acc = tg[cl];
-#pragma unroll 8
+#pragma unroll 16
           for (int q = 0; q < kw; ++q) acc = fma(-Lv[cps[q] + p], Xs[q][cl], acc);
           tg[cl] = acc;
           p += dp;
