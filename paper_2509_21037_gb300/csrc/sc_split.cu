@@ -407,19 +407,38 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
       for (int p0 = 0; p0 < kw; p0 += 8) {
         const int pe = min(p0 + 8, kw);
         if (warp == tri && lane < wk) {
-          for (int q = p0; q < pe; ++q) {
-            const double xq = Xs[q][lane] * id[kb + q];
-            Xs[q][lane] = xq;
-            const double *Lc = Lv + cps[q];
-            for (int r = q + 1; r < pe; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
+          if (pe - p0 == 8) {                 // a full piece: its column of X in registers
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = Xs[p0 + i][lane];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              x[i] *= id[kb + p0 + i];
+              const double *Lc = Lv + cps[p0 + i] + kb + p0;
+#pragma unroll
+              for (int r = i + 1; r < 8; ++r) x[r] = fma(-Lc[r], x[i], x[r]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Xs[p0 + i][lane] = x[i];
+          } else {
+            for (int q = p0; q < pe; ++q) {
+              const double xq = Xs[q][lane] * id[kb + q];
+              Xs[q][lane] = xq;
+              const double *Lc = Lv + cps[q];
+              for (int r = q + 1; r < pe; ++r) Xs[r][lane] = fma(-Lc[kb + r], xq, Xs[r][lane]);
+            }
           }
         }
         __syncthreads();
-        if (pe < kw) {
+        if (pe < kw) {                        // then pe == p0 + 8
           if (lane < wk) {
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = Xs[p0 + i][lane];
             for (int r = pe + ((warp - tri) & 3); r < kw; r += kThreads / 32) {
               double xr = Xs[r][lane];
-              for (int q = p0; q < pe; ++q) xr = fma(-Lv[cps[q] + kb + r], Xs[q][lane], xr);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) xr = fma(-Lv[cps[p0 + i] + kb + r], x[i], xr);
               Xs[r][lane] = xr;
             }
           }
