@@ -25,6 +25,7 @@ namespace sc {
 constexpr int kChunk = 32;      // column chunk width of the TRSM / SYRK tasks
 constexpr int kTile = 32;       // F tile edge
 constexpr int kThreads = 128;   // threads per CTA of the assembly kernels
+constexpr int kGridSMs = 152;   // SMs of a GB300: the round length of the TRSM task order (sc_plan.cpp)
 
 // bits of the workspace status word
 enum : uint32_t { kStatusNotSpd = 1u, kStatusTimeout = 2u };

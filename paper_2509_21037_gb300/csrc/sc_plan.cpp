@@ -543,6 +543,18 @@ sc_status build_plan(sc_ctx *ctx, int32_t nsub, const sc_subdomain_desc *d) {
   };
   {
     auto o = order_by(trsm_cost, trsm_var, trsm_wave);
+    // The TRSM of a batch is about one wave of resident CTAs, so what the launch
+    // costs is its busiest SM.  With CTAs handed to the SMs in index order, a
+    // largest-first list gives the low-numbered SMs the larger task of every
+    // round; reversing every other round of kGridSMs tasks (a snake) pairs
+    // larger with smaller ones.  Results do not depend on the order.
+    for (size_t g0 = 0; g0 < o.size();) {
+      size_t g1 = g0;
+      while (g1 < o.size() && trsm_wave[o[g1]] == trsm_wave[o[g0]] && trsm_var[o[g1]] == trsm_var[o[g0]]) ++g1;
+      for (size_t r0 = g0, rnd = 0; r0 < g1; r0 += kGridSMs, ++rnd)
+        if (rnd & 1) std::reverse(o.begin() + r0, o.begin() + std::min(g1, r0 + (size_t)kGridSMs));
+      g0 = g1;
+    }
     groups(trsm_var, trsm_wave, o, 0);
     std::vector<TrsmTask> t2(trsm.size());
     for (size_t k = 0; k < o.size(); ++k) t2[k] = trsm[o[k]];
