@@ -85,6 +85,9 @@ def check_bounds(T: dict, sizes, stats, tile_subs=()) -> None:
             assert 0 <= base and base + ws <= ydbl
     for e in T["seeds"]:
         assert 0 <= e["y_off"] < ydbl and np.isfinite(e["value"]) and e["value"] != 0.0
+    # every (subdomain, 32-column chunk) has exactly one TRSM task, whatever the order
+    chunks = sorted((int(t["sub"]), int(t["c_lo"])) for t in T["trsm"])
+    assert chunks == [(i, 32 * q) for i, sd in enumerate(subs) for q in range((int(sd["m"]) + 31) // 32)]
     for t in T["trsm"]:
         sd = subs[t["sub"]]
         assert 0 < t["w"] <= 32 and t["c_lo"] + t["w"] <= sd["m"]

@@ -679,3 +679,37 @@ def test_add_symmetric_batch_matches_pack():
     for e in entries:
         plan.add_symmetric(one, *e)
     assert torch.equal(one, want)
+
+
+def test_trsm_tasks_in_snake_order_of_largest_first():
+    """The planner hands the FP64 TRSM tasks out largest first by its cost
+    estimate (32 lanes x (kw^2 + 2 kw rows below) per nonempty 32-row block,
+    plus 1e3 per supernode in the list), with every other round of 152 tasks
+    reversed (one round per SM of a GB300): undoing the reversals gives a
+    non-increasing cost sequence, and the odd rounds run smallest first."""
+    prob = synth.make_config(2)
+    fs = host.factorize_problem(prob.subdomains)
+    plan = sc.Plan(fs, prob.n_dual)
+    T = pe.export_plan(plan)
+    pe.check_bounds(T, plan.sizes, plan.stats)
+    sns, cuts = T["sns"], T["cuts"]
+    cost = []
+    for t in T["trsm"]:
+        lst = T["trsm_list"][t["list_off"]:t["list_off"] + t["list_len"]]
+        c_lo, c_hi = int(t["c_lo"]), int(t["c_lo"]) + int(t["w"])
+        exe = 0
+        for si in lst:
+            s = sns[si]
+            a, b = max(int(s["jlo"]), c_lo), min(int(s["jhi"]), c_hi)
+            ns, nrow = int(s["ns"]), int(s["ns"]) + int(s["rs"])
+            for kb in range(0, ns, 32):
+                if min(b, int(cuts[int(s["cut_off"]) + kb // 32])) - a <= 0:
+                    continue
+                kw = min(32, ns - kb)
+                exe += 32 * (kw * kw + 2 * kw * (nrow - kb - kw))
+        cost.append(exe + 1000 * int(t["list_len"]))
+    assert len(cost) > 4 * 152
+    rounds = [cost[r:r + 152] for r in range(0, len(cost), 152)]
+    unsnaked = [c for k, r in enumerate(rounds) for c in (r[::-1] if k % 2 else r)]
+    assert all(x >= y for x, y in zip(unsnaked, unsnaked[1:]))
+    assert any(r[0] < r[-1] for r in rounds[1::2])
