@@ -471,10 +471,29 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
         const int ra = r0 + g, rb = r0 + g + 8;
         const bool va = ra < nb, vb = rb < nb;
         const int ea = va ? lexp[base + ra] : 0, eb = vb ? lexp[base + rb] : 0;
+        // this lane's two target rows (a pruned row through its map), looked up once per m-tile
+        double *tga = nullptr, *tgb = nullptr;
+        if (va) {
+          const int p = kb + kw + ra;
+          tga = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
+        }
+        if (vb) {
+          const int p = kb + kw + rb;
+          tgb = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
+        }
         if (!(pre && mt == warp)) load_afr(mt);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
           if (8 * nt >= wk) break;                   // uniform across the warp
+          // the targets' current values, loaded before the products so that
+          // their latency overlaps the MMAs
+          double yv[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const bool vr = (r & 2) ? vb : va;
+            const int col = 8 * nt + 2 * tg + (r & 1);
+            yv[r] = (vr && col < wk) ? ((r & 2) ? tgb : tga)[col] : 0.0;
+          }
           Groups<S> gr[4];
 #pragma unroll
           for (int d = 0; d < S; ++d) {
@@ -494,18 +513,17 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(
           }
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int rr = (r & 2) ? rb : ra;
+            const bool vr = (r & 2) ? vb : va;
             const int col = 8 * nt + 2 * tg + (r & 1);
-            if (rr < nb && col < wk) {
-              const int p = kb + kw + rr;
+            if (vr && col < wk) {
               const int e = (((r & 2) ? eb : ea) - 1022) + (emaxX[col] - 1022);
               // one conversion and one FMA on the FP64 pipe: both power-of-two
               // scalings folded into a single exponent
               const double v = (double)gr[r].block_int();
               const int eb = e + Groups<S>::kBlockShift;
-              double *tgt = (p < s.ns) ? (Ys + (int64_t)p * ws) : (Y + rm[p - s.ns] + colsh);
-              if (eb >= -1022 && eb <= 1023) tgt[col] = fma(-v, pow2i(eb), tgt[col]);
-              else tgt[col] -= ldexp(v, eb);
+              double *tgt = (r & 2) ? tgb : tga;
+              if (eb >= -1022 && eb <= 1023) tgt[col] = fma(-v, pow2i(eb), yv[r]);
+              else tgt[col] = yv[r] - ldexp(v, eb);
             }
           }
         }
