@@ -321,9 +321,10 @@ __global__ void __launch_bounds__(kThreads, (S <= 5 ? 4 : 3)) syrk_split_kernel(
 // bounds, shared memory) and of L's rows (pre-cut by lpack_kernel), combined
 // exactly in integers and subtracted from Y in FP64.
 template <int S>
-// 6 resident CTAs for up to 5 digits (the TRSM is latency-bound: more warps
-// hide the L digit and Y loads), 4 for 6 and 7 digits (their fragments would spill)
-__global__ void __launch_bounds__(kThreads, (S <= 5 ? 6 : 4)) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
+// 6 resident CTAs for up to 4 digits (the TRSM is latency-bound: more warps
+// hide the L digit and Y loads), 5 for 5 digits (at 6 its registers spill), 4 for
+// 6 and 7 digits (their fragments would spill)
+__global__ void __launch_bounds__(kThreads, (S <= 4 ? 6 : S == 5 ? 5 : 4)) trsm_split_kernel(const PlanPtrs P, const double *__restrict__ Lv,
                                                               const double *__restrict__ invd,
                                                               const __nv_bfloat16 *__restrict__ Ld,
                                                               const int16_t *__restrict__ lexp, int64_t ld_rows,
